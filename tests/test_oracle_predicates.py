@@ -1,0 +1,182 @@
+"""Pins the oracle's perturbed predicates to their definition.
+
+The perturbed point i is x~ = x + a z + a^2 y, y~ = y + b z + eta_i,
+z~ = z + gam_i with a >> b >> gam_0 >> gam_1 >> ... >> eta_0 >> eta_1 >> ...
+(i = input index); a predicate's sign is that of its largest monomial.  Here
+each predicate is expanded symbolically with sympy and its leading monomial is
+picked by reading exponent vectors from the smallest variable upwards -- a
+generic formulation that shares nothing with the oracle's C engine.
+"""
+import numpy as np
+import pytest
+
+sympy = pytest.importorskip("sympy")
+
+import oracle  # noqa: E402
+
+A, B = sympy.symbols("a b")
+
+
+def _gens(ids):
+    order = sorted(set(int(i) for i in ids))
+    g = {i: sympy.Symbol(f"g{i}") for i in order}
+    h = {i: sympy.Symbol(f"h{i}") for i in order}
+    # largest variable first: a, b, gam by index, eta by index
+    gens = [A, B] + [g[i] for i in order] + [h[i] for i in order]
+    return g, h, gens
+
+
+def _pert(p, i, g, h):
+    x, y, z = (int(v) for v in p)
+    return (x + A * z + A**2 * y, y + B * z + h[i], z + g[i])
+
+
+def _lead_sign(expr, gens):
+    poly = sympy.Poly(sympy.expand(expr), *gens)
+    terms = [(m, c) for m, c in poly.terms() if c != 0]
+    if not terms:
+        return 0
+    # the larger monomial has the smaller exponent at the first difference,
+    # reading from the last (smallest) variable
+    m, c = min(terms, key=lambda t: tuple(reversed(t[0])))
+    return 1 if c > 0 else -1
+
+
+def _cross2(P, Q, R, k):
+    return (Q[0] - P[0]) * (R[k] - P[k]) - (R[0] - P[0]) * (Q[k] - P[k])
+
+
+def ref_turn(pts, ids):
+    g, h, gens = _gens(ids)
+    P, Q, R = (_pert(pts[j], ids[j], g, h) for j in range(3))
+    return _lead_sign(_cross2(P, Q, R, 1), gens)
+
+
+def ref_time_cmp(pts, ids):
+    if set(int(i) for i in ids[:3]) == set(int(i) for i in ids[3:]):
+        return 0
+    g, h, gens = _gens(ids)
+    P = [_pert(pts[j], ids[j], g, h) for j in range(6)]
+    Z1, Y1 = _cross2(P[0], P[1], P[2], 2), _cross2(P[0], P[1], P[2], 1)
+    Z2, Y2 = _cross2(P[3], P[4], P[5], 2), _cross2(P[3], P[4], P[5], 1)
+    # t1 - t2 = (Z1 Y2 - Z2 Y1) / (Y1 Y2)
+    return _lead_sign(Z1 * Y2 - Z2 * Y1, gens) * _lead_sign(Y1 * Y2, gens)
+
+
+def ref_orient3d(pts, ids):
+    g, h, gens = _gens(ids)
+    P = [_pert(pts[j], ids[j], g, h) for j in range(4)]
+    M = sympy.Matrix([[P[r][c] - P[0][c] for c in range(3)] for r in range(1, 4)])
+    return _lead_sign(M.det(method="berkowitz"), gens)
+
+
+def _distinct(rows):
+    return len(set(map(tuple, rows))) == len(rows)
+
+
+def _cases(k, count, seed):
+    """Tuples of k distinct points: tiny boxes (heavy degeneracy), structured
+    degenerate sets, and wide random ones; ids are a random permutation."""
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < count:
+        kind = len(out) % 5
+        if kind == 0:
+            p = rng.integers(-2, 3, size=(k, 3))
+        elif kind == 1:  # all on one line through the origin, varied steps
+            d = rng.integers(-3, 4, size=3)
+            if not d.any():
+                continue
+            p = np.outer(rng.choice(np.arange(-6, 7), size=k, replace=False), d)
+        elif kind == 2:  # a coordinate plane with small values
+            p = rng.integers(-3, 4, size=(k, 3))
+            p[:, rng.integers(0, 3)] = rng.integers(-2, 3)
+        elif kind == 3:  # shared x, extreme magnitudes
+            p = rng.choice([-(1 << 20), -1, 0, 1, (1 << 20) - 1], size=(k, 3))
+        else:
+            p = rng.integers(-(1 << 20), 1 << 20, size=(k, 3))
+        if not _distinct(p):
+            continue
+        ids = rng.permutation(50)[:k]
+        out.append((p.astype(np.int32), ids.astype(np.int32)))
+    return out
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_turn_sign_matches_definition(seed):
+    for p, ids in _cases(3, 150, seed):
+        assert oracle.turn_sign(p, ids) == ref_turn(p, ids), (p.tolist(), ids.tolist())
+
+
+def test_turn_never_zero_and_antisymmetric():
+    for p, ids in _cases(3, 200, 3):
+        s = oracle.turn_sign(p, ids)
+        assert s != 0
+        assert oracle.turn_sign(p[[1, 0, 2]], ids[[1, 0, 2]]) == -s
+
+
+@pytest.mark.parametrize("seed", [4, 5])
+def test_time_cmp_matches_definition(seed):
+    rng = np.random.default_rng(seed)
+    n_checked = 0
+    for p, ids in _cases(6, 140, seed):
+        if n_checked % 4 == 0:  # two triples sharing two points (the algorithm's usual case)
+            p = p[[0, 1, 2, 0, 1, 3]]
+            ids = ids[[0, 1, 2, 0, 1, 3]]
+        elif n_checked % 4 == 1:  # sharing one point
+            p = p[[0, 1, 2, 0, 3, 4]]
+            ids = ids[[0, 1, 2, 0, 3, 4]]
+        if not (_distinct(p[:3]) and _distinct(p[3:])):
+            continue
+        n_checked += 1
+        got = oracle.time_cmp(p, ids)
+        assert got == ref_time_cmp(p, ids), (p.tolist(), ids.tolist())
+        # antisymmetry and invariance under reordering a triple
+        assert oracle.time_cmp(np.concatenate([p[3:], p[:3]]), np.concatenate([ids[3:], ids[:3]])) == -got
+        perm = rng.permutation(3)
+        assert oracle.time_cmp(np.concatenate([p[:3][perm], p[3:]]), np.concatenate([ids[:3][perm], ids[3:]])) == got
+    assert n_checked > 100
+
+
+def test_time_cmp_same_set_is_tie():
+    for p, ids in _cases(3, 50, 6):
+        q = np.concatenate([p, p[[2, 0, 1]]])
+        j = np.concatenate([ids, ids[[2, 0, 1]]])
+        assert oracle.time_cmp(q, j) == 0
+
+
+def test_time_cmp_distinct_triples_never_tie():
+    for p, ids in _cases(6, 300, 7):
+        if set(ids[:3].tolist()) == set(ids[3:].tolist()):
+            continue
+        if _distinct(p[:3]) and _distinct(p[3:]):
+            assert oracle.time_cmp(p, ids) != 0
+
+
+@pytest.mark.parametrize("seed", [8, 9])
+def test_orient3d_matches_definition(seed):
+    for p, ids in _cases(4, 120, seed):
+        s = oracle.orient3d_sign(p, ids)
+        assert s != 0
+        assert s == ref_orient3d(p, ids), (p.tolist(), ids.tolist())
+
+
+def test_time_cmp_plain_rationals_in_general_position():
+    """Away from ties the perturbed order is the plain order of Z/Y."""
+    from fractions import Fraction
+
+    rng = np.random.default_rng(10)
+    done = 0
+    while done < 400:
+        p = rng.integers(-(1 << 20), 1 << 20, size=(6, 3)).astype(np.int64)
+        t = []
+        for k in (0, 3):
+            a, b, c = p[k], p[k + 1], p[k + 2]
+            Y = (b[0] - a[0]) * (c[1] - a[1]) - (c[0] - a[0]) * (b[1] - a[1])
+            Z = (b[0] - a[0]) * (c[2] - a[2]) - (c[0] - a[0]) * (b[2] - a[2])
+            t.append(Fraction(int(Z), int(Y)) if Y else None)
+        if None in t or t[0] == t[1]:
+            continue
+        done += 1
+        want = 1 if t[0] > t[1] else -1
+        assert oracle.time_cmp(p.astype(np.int32), np.arange(6, dtype=np.int32)) == want
