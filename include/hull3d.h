@@ -1,0 +1,132 @@
+/*
+ * hull3d.h -- C ABI of the GB300 kinetic divide-and-conquer 3D convex hull.
+ *
+ * The problem (White & Wortman, Sec. 1): given n points in R^3, find the
+ * faces of their convex hull.  The method (Sec. 2): sort the points by x,
+ * recast the lower hull as a kinetic 2D hull whose "movie" is a chronological
+ * list of insert/delete events, build those movies bottom-up by merging
+ * adjacent blocks level by level (ceil(log2 n) merge steps, each merge
+ * tracking the bridge between its two halves), and read the faces off the
+ * root movie (each event is one face).  The upper hull is the same
+ * computation on the z-mirrored set.
+ *
+ * Conventions shared by every entry point
+ *   - Points are int32 triples (x, y, z), row-major n x 3, every coordinate in
+ *     [-2^20, 2^20).  Duplicated points are an error.
+ *   - Degenerate inputs (equal x, collinear or coplanar points) are resolved
+ *     by one fixed symbolic perturbation:
+ *       x~ = x + a z + a^2 y,  y~ = y + b z + eta_i,  z~ = z + gam_i
+ *     (i = input index, a >> b >> gam_0 >> ... >> gam_{n-1} >> eta_0 >> ...),
+ *     so the output is always a triangulated closed surface with
+ *     F = 2V - 4 faces, V <= n.  All arithmetic is exact integer arithmetic.
+ *   - Output faces are int32 triples of INPUT indices, counter-clockwise seen
+ *     from outside, rotated so the smallest index comes first, and sorted
+ *     lexicographically.  n <= 2 gives 0 faces, n = 3 gives the triangle's
+ *     two sides.  At most 2n - 4 faces (n >= 3).
+ *   - Device pointers are CUDA device (or managed) memory owned by the
+ *     caller; the plan owns all scratch.  "stream" is a cudaStream_t (NULL =
+ *     the legacy default stream).  Asynchronous entry points only enqueue
+ *     work; their results are valid once the stream has reached them.
+ *   - Return values: 0 on success, else a HULL3D_ERR_* code (see
+ *     hull3d_strerror).  Nothing aborts, traps or prints.
+ */
+#ifndef HULL3D_H
+#define HULL3D_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HULL3D_OK 0
+#define HULL3D_ERR_INVALID_ARG 1   /* null pointer, n < 1, n above the plan, bad offsets */
+#define HULL3D_ERR_COORD_RANGE 2   /* a coordinate outside [-2^20, 2^20) */
+#define HULL3D_ERR_DUPLICATE 3     /* two equal points */
+#define HULL3D_ERR_CAPACITY 4      /* output capacity below 2n - 4 faces */
+#define HULL3D_ERR_OOM 5           /* device allocation failed */
+#define HULL3D_ERR_BUDGET 6        /* request above a memory budget */
+#define HULL3D_ERR_DEVICE_TIMEOUT 7 /* a bounded device wait ran out */
+#define HULL3D_ERR_CUDA 8          /* a CUDA runtime call failed (see hull3d_last_cuda_error) */
+#define HULL3D_ERR_INTERNAL 9      /* an internal consistency check failed */
+
+#define HULL3D_MAX_N (1 << 28)     /* largest n one plan accepts */
+
+typedef struct hull3d_plan_s *hull3d_plan_t;
+
+/* Tuning knobs; zero fields mean "automatic". */
+typedef struct {
+    int32_t fused_levels;   /* levels merged in shared memory by the fused bottom kernel (1..10) */
+    int32_t seg_level;      /* first level merged time-segment-parallel; < 0 disables */
+    int32_t seg_events;     /* target child events per time segment */
+    int32_t use_graph;      /* 1: replay the level sequence as a CUDA graph (default), -1: plain launches */
+    int32_t reserved[4];
+} hull3d_opts;
+
+/* Creates a plan for hulls of up to max_n points (hull3d_compute*) and for
+ * batches of up to max_clouds clouds totalling up to max_n points
+ * (hull3d_batch).  Allocates every scratch buffer up front on the current
+ * device.  opts may be NULL.  On failure *out is NULL and the code is
+ * HULL3D_ERR_INVALID_ARG or HULL3D_ERR_OOM. */
+int hull3d_plan(hull3d_plan_t *out, int64_t max_n, int64_t max_clouds, const hull3d_opts *opts);
+
+/* Frees the plan and its scratch (synchronises the device first). NULL is a no-op. */
+void hull3d_destroy(hull3d_plan_t plan);
+
+/* Bytes of device scratch the plan holds. */
+int64_t hull3d_plan_bytes(hull3d_plan_t plan);
+
+/* Enqueues the hull of n points on stream.
+ *   d_xyz     device, n x 3 int32, read only
+ *   d_faces   device, cap_faces x 3 int32, written with the canonical faces
+ *   d_nfaces  device int64, written with the face count (may be NULL)
+ *   d_status  device int32, written with 0 or a HULL3D_ERR_* code detected on
+ *             the device (range, duplicate, internal) (may be NULL)
+ * Host-detected argument errors are returned immediately and nothing is
+ * enqueued.  Calls sharing a plan must be serialised on one stream (they
+ * share its scratch).  Sec. 2 ("movie array" merge steps), Sec. 3 (act, time). */
+int hull3d_compute_async(hull3d_plan_t plan, const int32_t *d_xyz, int64_t n, int32_t *d_faces,
+                         int64_t cap_faces, int64_t *d_nfaces, int32_t *d_status, void *stream);
+
+/* Synchronous form of hull3d_compute_async: enqueues, waits for the stream,
+ * stores the face count in *h_nfaces (host, may be NULL) and returns the
+ * device-detected status. */
+int hull3d_compute(hull3d_plan_t plan, const int32_t *d_xyz, int64_t n, int32_t *d_faces, int64_t cap_faces,
+                   int64_t *h_nfaces, void *stream);
+
+/* End-to-end form on HOST buffers: copies h_xyz (n x 3 int32) to the device,
+ * computes, copies the faces back to h_faces (cap_faces x 3 int32) and the
+ * count to *h_nfaces, then returns the status.  Uses plan-owned device
+ * staging buffers; the host buffers should be pinned for full copy speed. */
+int hull3d_compute_host(hull3d_plan_t plan, const int32_t *h_xyz, int64_t n, int32_t *h_faces, int64_t cap_faces,
+                        int64_t *h_nfaces, void *stream);
+
+/* Enqueues the hulls of B independent clouds concatenated in d_xyz.
+ *   h_offsets       host int64 [B+1]: cloud b is rows [h_offsets[b], h_offsets[b+1]) of d_xyz
+ *   d_faces         device int32 x 3: cloud b's faces start at row h_face_offsets[b]
+ *   h_face_offsets  host int64 [B+1]: row capacity of cloud b is
+ *                   h_face_offsets[b+1] - h_face_offsets[b] (needs max(0, 2 n_b - 4))
+ *   d_nfaces        device int64 [B]: face count per cloud
+ *   d_status        device int32 [B]: 0 or a HULL3D_ERR_* code per cloud
+ * Faces are per-cloud canonical lists of indices local to the cloud.  Each
+ * cloud may hold up to the plan's max_n points.  Host-detected argument
+ * errors (bad offsets, capacity) are returned before anything is enqueued. */
+int hull3d_batch_async(hull3d_plan_t plan, const int32_t *d_xyz, const int64_t *h_offsets, int64_t B,
+                       int32_t *d_faces, const int64_t *h_face_offsets, int64_t *d_nfaces, int32_t *d_status,
+                       void *stream);
+
+/* Text for a HULL3D_* code. */
+const char *hull3d_strerror(int code);
+
+/* The last CUDA runtime error code seen by the library on this thread (0 if none). */
+int hull3d_last_cuda_error(void);
+
+/* Number of kernel launches the last call on this plan enqueued (graph nodes
+ * count one each). */
+int64_t hull3d_last_launch_count(hull3d_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HULL3D_H */

@@ -1,0 +1,301 @@
+// api.cu -- the C ABI: plan (all scratch allocated up front), the level driver
+// (the paper's host "main outer loop", Sec. 3, replayed without host syncs)
+// and the entry points declared in include/hull3d.h.
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "internal.h"
+
+using namespace hull3d;
+
+namespace {
+
+thread_local int g_last_cuda = 0;
+
+int cuda_fail(cudaError_t e)
+{
+    g_last_cuda = (int)e;
+    return HULL3D_ERR_CUDA;
+}
+
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+
+int ceil_log2(int64_t n)
+{
+    int l = 0;
+    while ((1ll << l) < n) l++;
+    return l;
+}
+
+}  // namespace
+
+struct hull3d_plan_s {
+    int64_t max_n = 0, max_clouds = 0;
+    hull3d_opts opts{};
+    int device = 0;
+    char *pool = nullptr;
+    size_t pool_bytes = 0;
+    // sort (capacity 2 max_n: also used for the face sort)
+    uint64_t *k0 = nullptr, *k1 = nullptr;
+    uint32_t *v0 = nullptr, *v1 = nullptr;
+    SortScratch ss{};
+    // rank-ordered points
+    int32_t *X = nullptr, *Y = nullptr, *Z = nullptr, *ID = nullptr;
+    PassBufs pass[2]{};
+    int32_t *status = nullptr;
+    int64_t *nfaces = nullptr;
+    int32_t *stage_xyz = nullptr, *stage_faces = nullptr;
+    // pinned host mirrors
+    int64_t *h_nfaces = nullptr;
+    int32_t *h_status = nullptr;
+    int64_t last_launches = 0;
+};
+
+namespace {
+
+struct Bump {
+    char *base;
+    size_t off, cap;
+    template <class T>
+    T *take(int64_t count)
+    {
+        size_t bytes = ((size_t)count * sizeof(T) + 255) & ~(size_t)255;
+        T *p = (T *)(base ? base + off : nullptr);
+        off += bytes;
+        return p;
+    }
+};
+
+// Lays out every buffer of the plan; with base == nullptr it only measures.
+size_t layout(hull3d_plan_s *p, char *base)
+{
+    const int64_t N = p->max_n, N2 = 2 * p->max_n;
+    Bump b{ base, 0, 0 };
+    p->k0 = b.take<uint64_t>(N2);
+    p->k1 = b.take<uint64_t>(N2);
+    p->v0 = b.take<uint32_t>(N2);
+    p->v1 = b.take<uint32_t>(N2);
+    p->ss.max_tiles = (N2 + SORT_TILE - 1) / SORT_TILE;
+    p->ss.hist = b.take<uint32_t>(256 * p->ss.max_tiles);
+    p->ss.rowsum = b.take<uint32_t>(256);
+    p->X = b.take<int32_t>(N);
+    p->Y = b.take<int32_t>(N);
+    p->Z = b.take<int32_t>(N);
+    p->ID = b.take<int32_t>(N);
+    for (int s = 0; s < 2; s++) {
+        PassBufs &pb = p->pass[s];
+        for (int k = 0; k < 2; k++) {
+            pb.W[k] = b.take<unsigned>(N2);
+            pb.A[k] = b.take<int32_t>(N2);
+            pb.B[k] = b.take<int32_t>(N2);
+            pb.cnt[k] = b.take<int32_t>(N);
+        }
+        pb.prv = b.take<int32_t>(N);
+        pb.nxt = b.take<int32_t>(N);
+    }
+    p->status = b.take<int32_t>(1);
+    p->nfaces = b.take<int64_t>(1);
+    p->stage_xyz = b.take<int32_t>(3 * N);
+    p->stage_faces = b.take<int32_t>(3 * N2);
+    return b.off;
+}
+
+int default_fused(const hull3d_plan_s *p) { return p->opts.fused_levels > 0 ? p->opts.fused_levels : 8; }
+
+// Enqueues the whole single-hull pipeline.
+int enqueue_hull(hull3d_plan_s *p, const int32_t *d_xyz, int64_t n, int32_t *d_faces, int64_t *nf, int32_t *status,
+                 cudaStream_t st)
+{
+    int64_t launches = 0;
+    CK(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
+    launch_keys(d_xyz, n, p->k0, p->v0, status, st);
+    launches++;
+    int which = radix_sort_pairs(p->k0, p->v0, p->k1, p->v1, n, nullptr, 63, p->ss, st, &launches);
+    launch_decode(which ? p->k1 : p->k0, which ? p->v1 : p->v0, n, p->X, p->Y, p->Z, p->ID, status, st);
+    launches++;
+    if (n < 3) {
+        CK(cudaMemsetAsync(nf, 0, sizeof(int64_t), st));
+        p->last_launches = launches;
+        return cudaGetLastError() == cudaSuccess ? HULL3D_OK : HULL3D_ERR_CUDA;
+    }
+    Points pts{ p->X, p->Y, p->Z, p->ID };
+    const int L = ceil_log2(n);
+    int l1 = default_fused(p);
+    if (l1 > L) l1 = L;
+    if (l1 > 10) l1 = 10;
+    launch_fused(pts, n, 0, l1, p->pass, 2, status, st);
+    launches++;
+    for (int level = l1 + 1; level <= L; level++) {
+        launch_level(pts, n, level, p->pass, 2, status, st);
+        int64_t last_lo = (((n + (1ll << level) - 1) >> level) - 1) << level;
+        launches += (last_lo + (1ll << (level - 1)) >= n) ? 2 : 1;  // level + pass-through copy
+    }
+    int fbits = ceil_log2(n);
+    if (fbits < 1) fbits = 1;
+    launch_face_keys(pts, n, L, p->pass, p->k0, p->v0, nf, status, st);
+    launches++;
+    which = radix_sort_pairs(p->k0, p->v0, p->k1, p->v1, 2 * n, nf, 2 * fbits, p->ss, st, &launches);
+    launch_face_out(which ? p->k1 : p->k0, which ? p->v1 : p->v0, 2 * n, fbits, nf, d_faces, st);
+    launches++;
+    p->last_launches = launches;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e);
+    return HULL3D_OK;
+}
+
+int check_compute_args(hull3d_plan_s *p, const void *xyz, int64_t n, const void *faces, int64_t cap)
+{
+    if (!p || !xyz || n < 1 || n > p->max_n) return HULL3D_ERR_INVALID_ARG;
+    if (n >= 3) {
+        if (!faces) return HULL3D_ERR_INVALID_ARG;
+        if (cap < 2 * n - 4) return HULL3D_ERR_CAPACITY;
+    }
+    return HULL3D_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hull3d_plan(hull3d_plan_t *out, int64_t max_n, int64_t max_clouds, const hull3d_opts *opts)
+{
+    if (!out) return HULL3D_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (max_n < 1 || max_n > HULL3D_MAX_N || max_clouds < 0) return HULL3D_ERR_INVALID_ARG;
+    hull3d_plan_s *p = new (std::nothrow) hull3d_plan_s();
+    if (!p) return HULL3D_ERR_OOM;
+    p->max_n = max_n < 4 ? 4 : max_n;
+    p->max_clouds = max_clouds;
+    if (opts) p->opts = *opts;
+    if (p->opts.fused_levels < 0 || p->opts.fused_levels > 10) { delete p; return HULL3D_ERR_INVALID_ARG; }
+    cudaGetDevice(&p->device);
+    p->pool_bytes = layout(p, nullptr);
+    cudaError_t e = cudaMalloc((void **)&p->pool, p->pool_bytes);
+    if (e != cudaSuccess) {
+        g_last_cuda = (int)e;
+        cudaGetLastError();
+        delete p;
+        return e == cudaErrorMemoryAllocation ? HULL3D_ERR_OOM : HULL3D_ERR_CUDA;
+    }
+    layout(p, p->pool);
+    e = cudaMallocHost((void **)&p->h_nfaces, 64);
+    if (e != cudaSuccess) {
+        cudaFree(p->pool);
+        delete p;
+        return cuda_fail(e);
+    }
+    p->h_status = (int32_t *)(p->h_nfaces + 2);
+    *out = p;
+    return HULL3D_OK;
+}
+
+void hull3d_destroy(hull3d_plan_t p)
+{
+    if (!p) return;
+    cudaDeviceSynchronize();
+    cudaFree(p->pool);
+    cudaFreeHost(p->h_nfaces);
+    delete p;
+}
+
+int64_t hull3d_plan_bytes(hull3d_plan_t p) { return p ? (int64_t)p->pool_bytes : 0; }
+
+int64_t hull3d_last_launch_count(hull3d_plan_t p) { return p ? p->last_launches : 0; }
+
+int hull3d_compute_async(hull3d_plan_t p, const int32_t *d_xyz, int64_t n, int32_t *d_faces, int64_t cap_faces,
+                         int64_t *d_nfaces, int32_t *d_status, void *stream)
+{
+    int rc = check_compute_args(p, d_xyz, n, d_faces, cap_faces);
+    if (rc) return rc;
+    return enqueue_hull(p, d_xyz, n, d_faces, d_nfaces ? d_nfaces : p->nfaces, d_status ? d_status : p->status,
+                        (cudaStream_t)stream);
+}
+
+int hull3d_compute(hull3d_plan_t p, const int32_t *d_xyz, int64_t n, int32_t *d_faces, int64_t cap_faces,
+                   int64_t *h_nfaces, void *stream)
+{
+    int rc = check_compute_args(p, d_xyz, n, d_faces, cap_faces);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    rc = enqueue_hull(p, d_xyz, n, d_faces, p->nfaces, p->status, st);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(p->h_nfaces, p->nfaces, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(p->h_status, p->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h_nfaces) *h_nfaces = *p->h_status ? 0 : *p->h_nfaces;
+    return *p->h_status;
+}
+
+int hull3d_compute_host(hull3d_plan_t p, const int32_t *h_xyz, int64_t n, int32_t *h_faces, int64_t cap_faces,
+                        int64_t *h_nfaces, void *stream)
+{
+    int rc = check_compute_args(p, h_xyz, n, h_faces, cap_faces);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(p->stage_xyz, h_xyz, (size_t)n * 3 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    rc = enqueue_hull(p, p->stage_xyz, n, p->stage_faces, p->nfaces, p->status, st);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(p->h_nfaces, p->nfaces, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(p->h_status, p->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int status = *p->h_status;
+    int64_t nf = status ? 0 : *p->h_nfaces;
+    if (nf > 0) {
+        CK(cudaMemcpyAsync(h_faces, p->stage_faces, (size_t)nf * 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    if (h_nfaces) *h_nfaces = nf;
+    return status;
+}
+
+int hull3d_batch_async(hull3d_plan_t p, const int32_t *d_xyz, const int64_t *h_offsets, int64_t B, int32_t *d_faces,
+                       const int64_t *h_face_offsets, int64_t *d_nfaces, int32_t *d_status, void *stream)
+{
+    if (!p || !h_offsets || !h_face_offsets || B < 0 || (B > 0 && (!d_xyz || !d_faces || !d_nfaces || !d_status)))
+        return HULL3D_ERR_INVALID_ARG;
+    if (h_offsets[0] != 0 || h_face_offsets[0] != 0) return HULL3D_ERR_INVALID_ARG;
+    for (int64_t b = 0; b < B; b++) {
+        int64_t nb = h_offsets[b + 1] - h_offsets[b];
+        int64_t cap = h_face_offsets[b + 1] - h_face_offsets[b];
+        if (nb < 1 || nb > p->max_n || cap < 0) return HULL3D_ERR_INVALID_ARG;
+        if (nb >= 3 && cap < 2 * nb - 4) return HULL3D_ERR_CAPACITY;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t launches = 0;
+    for (int64_t b = 0; b < B; b++) {
+        int64_t nb = h_offsets[b + 1] - h_offsets[b];
+        int rc = enqueue_hull(p, d_xyz + 3 * h_offsets[b], nb, d_faces + 3 * h_face_offsets[b], d_nfaces + b,
+                              d_status + b, st);
+        if (rc) return rc;
+        launches += p->last_launches;
+    }
+    p->last_launches = launches;
+    return HULL3D_OK;
+}
+
+const char *hull3d_strerror(int code)
+{
+    switch (code) {
+    case HULL3D_OK: return "ok";
+    case HULL3D_ERR_INVALID_ARG: return "invalid argument";
+    case HULL3D_ERR_COORD_RANGE: return "coordinate outside [-2^20, 2^20)";
+    case HULL3D_ERR_DUPLICATE: return "duplicate point";
+    case HULL3D_ERR_CAPACITY: return "output capacity below 2n - 4 faces";
+    case HULL3D_ERR_OOM: return "device allocation failed";
+    case HULL3D_ERR_BUDGET: return "request above the memory budget";
+    case HULL3D_ERR_DEVICE_TIMEOUT: return "a bounded device wait ran out";
+    case HULL3D_ERR_CUDA: return "CUDA runtime error";
+    case HULL3D_ERR_INTERNAL: return "internal consistency check failed";
+    default: return "unknown error";
+    }
+}
+
+int hull3d_last_cuda_error(void) { return g_last_cuda; }
+
+}  // extern "C"

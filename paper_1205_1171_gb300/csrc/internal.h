@@ -1,0 +1,67 @@
+// internal.h -- launchers shared between the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hull3d.h"
+
+namespace hull3d {
+
+// Scratch for the LSD radix sort of (uint64 key, uint32 value) pairs.
+struct SortScratch {
+    uint32_t *hist;     // 256 x max_tiles
+    uint32_t *rowsum;   // 256
+    int64_t max_tiles;
+};
+
+constexpr int SORT_TILE = 4096;  // keys per CTA tile (256 threads x 16)
+
+// Sorts keys/vals (n items, or *d_n items when d_n != NULL, n being the
+// capacity) by bits [0, bits) of the key.  Ping-pongs between (k0, v0) and
+// (k1, v1); returns 0 if the result ends in (k0, v0) and 1 otherwise.
+int radix_sort_pairs(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int64_t n, const int64_t *d_n,
+                     int bits, const SortScratch &s, cudaStream_t st, int64_t *launches);
+
+// A1: range check and key build: key = (x + 2^20) << 42 | (z + 2^20) << 21 | (y + 2^20).
+void launch_keys(const int32_t *xyz, int64_t n, uint64_t *keys, uint32_t *vals, int32_t *status, cudaStream_t st);
+
+// After the sort: decode the sorted keys to the rank-ordered SoA and flag duplicates.
+void launch_decode(const uint64_t *keys, const uint32_t *vals, int64_t n, int32_t *X, int32_t *Y, int32_t *Z,
+                   int32_t *ID, int32_t *status, cudaStream_t st);
+
+// Event-list storage of one pass: two ping-pong buffers (W with the insert flag, A, B) and counts by node lo.
+struct PassBufs {
+    unsigned *W[2];
+    int32_t *A[2], *B[2];
+    int32_t *cnt[2];
+    int32_t *prv, *nxt;
+};
+
+struct Points {
+    const int32_t *X, *Y, *Z, *ID;
+};
+
+// Level 1 (pairs) for both passes: links of each pair, empty movies.
+void launch_level1(int64_t n, PassBufs *passes, int npass, int32_t *status, cudaStream_t st);
+
+// Levels [l0 + 1, l1] fused in shared memory (block = 2^l1 ranks), reading level l0 from buffer l0 & 1.
+void launch_fused(const Points &pts, int64_t n, int l0, int l1, PassBufs *passes, int npass, int32_t *status,
+                  cudaStream_t st);
+
+// One level (>= 2), one thread per merge, global memory.
+void launch_level(const Points &pts, int64_t n, int level, PassBufs *passes, int npass, int32_t *status,
+                  cudaStream_t st);
+
+// Faces of the root movies of both passes (level L = ceil(log2 n) in buffer L & 1):
+// orient, rotate min-first, build the sort key (f0 << 28 | f1) and value f2.
+void launch_face_keys(const Points &pts, int64_t n, int level, PassBufs *passes, uint64_t *keys, uint32_t *vals,
+                      int64_t *d_nfaces, int32_t *status, cudaStream_t st);
+
+// Sorted face keys -> int32 x 3 output rows (key = f0 << fbits | f1, fbits = ceil(log2 n)).
+void launch_face_out(const uint64_t *keys, const uint32_t *vals, int64_t cap, int fbits, const int64_t *d_nfaces,
+                     int32_t *faces, cudaStream_t st);
+
+// Shared memory of the fused kernel for blocks of 2^l1 ranks.
+size_t fused_smem_bytes(int l1);
+
+}  // namespace hull3d

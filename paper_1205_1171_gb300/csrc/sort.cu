@@ -1,0 +1,225 @@
+// sort.cu -- A1 (validate + key) and A2 (radix sort by the perturbed x-order).
+//
+// The paper presorts the points by x before the merge levels (Sec. 2; the
+// `sort(P, n)` of the figure "Differences in list creation").  Under the
+// symbolic perturbation x~ = x + a z + a^2 y the x-order is the lexicographic
+// order of (x, z, y), so each point gets the 63-bit key
+//   (x + 2^20) << 42 | (z + 2^20) << 21 | (y + 2^20)
+// and a stable LSD radix sort (8-bit digits) orders the keys with the input
+// index as payload.  The sorted keys decode back to the coordinates, so no
+// gather of the input is needed afterwards; equal adjacent keys are duplicates.
+#include "internal.h"
+
+namespace hull3d {
+
+__device__ __forceinline__ void set_status(int32_t *status, int code) { atomicCAS(status, 0, code); }
+
+__global__ void k_keys(const int32_t *__restrict__ xyz, int64_t n, uint64_t *__restrict__ keys,
+                       uint32_t *__restrict__ vals, int32_t *status)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+    const int lo = -(1 << 20), hi = (1 << 20) - 1;
+    bool ok = x >= lo && x <= hi && y >= lo && y <= hi && z >= lo && z <= hi;
+    if (!ok) set_status(status, HULL3D_ERR_COORD_RANGE);
+    uint64_t bx = (uint64_t)(x - lo) & 0x1fffff, by = (uint64_t)(y - lo) & 0x1fffff, bz = (uint64_t)(z - lo) & 0x1fffff;
+    keys[i] = (bx << 42) | (bz << 21) | by;
+    vals[i] = (uint32_t)i;
+}
+
+void launch_keys(const int32_t *xyz, int64_t n, uint64_t *keys, uint32_t *vals, int32_t *status, cudaStream_t st)
+{
+    if (n <= 0) return;
+    k_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(xyz, n, keys, vals, status);
+}
+
+__global__ void k_decode(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t n,
+                         int32_t *__restrict__ X, int32_t *__restrict__ Y, int32_t *__restrict__ Z,
+                         int32_t *__restrict__ ID, int32_t *status)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t k = keys[i];
+    const int lo = -(1 << 20);
+    X[i] = (int)((k >> 42) & 0x1fffff) + lo;
+    Z[i] = (int)((k >> 21) & 0x1fffff) + lo;
+    Y[i] = (int)(k & 0x1fffff) + lo;
+    ID[i] = (int32_t)vals[i];
+    if (i > 0 && keys[i - 1] == k) set_status(status, HULL3D_ERR_DUPLICATE);
+}
+
+void launch_decode(const uint64_t *keys, const uint32_t *vals, int64_t n, int32_t *X, int32_t *Y, int32_t *Z,
+                   int32_t *ID, int32_t *status, cudaStream_t st)
+{
+    if (n <= 0) return;
+    k_decode<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(keys, vals, n, X, Y, Z, ID, status);
+}
+
+// ---------------------------------------------------------------------------
+// LSD radix sort, 8-bit digits, 3 kernels per pass:
+//   hist    per-tile digit histogram -> hist[digit * T + tile]
+//   rowscan per-digit exclusive scan over tiles, row totals -> rowsum[digit]
+//   scatter stable per-tile ranking (warp match + per-warp bases) and scatter
+// ---------------------------------------------------------------------------
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = SORT_TILE / RS_THREADS;  // 16
+constexpr int RS_WARPS = RS_THREADS / 32;
+
+__device__ __forceinline__ int64_t count_of(int64_t n, const int64_t *d_n) { return d_n ? *d_n : n; }
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t *__restrict__ keys, int64_t n,
+                                                        const int64_t *d_n, int shift, uint32_t *hist, int64_t T)
+{
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t cnt = count_of(n, d_n);
+    int64_t base = blockIdx.x * (int64_t)SORT_TILE;
+#pragma unroll 4
+    for (int it = 0; it < RS_ITEMS; it++) {
+        int64_t i = base + it * RS_THREADS + threadIdx.x;
+        if (i < cnt) atomicAdd(&h[(keys[i] >> shift) & 0xff], 1u);
+    }
+    __syncthreads();
+    hist[threadIdx.x * T + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(1024) k_rs_rowscan(uint32_t *hist, int64_t T, const int64_t *d_n, int64_t n,
+                                                     uint32_t *rowsum)
+{
+    __shared__ uint32_t wsum[32];
+    int64_t cnt = count_of(n, d_n);
+    int64_t Tu = (cnt + SORT_TILE - 1) / SORT_TILE;  // tiles in use
+    uint32_t *row = hist + blockIdx.x * T;
+    int per = (int)((Tu + 1023) / 1024);
+    int64_t b0 = threadIdx.x * (int64_t)per;
+    uint32_t s = 0;
+    for (int k = 0; k < per; k++)
+        if (b0 + k < Tu) s += row[b0 + k];
+    // block exclusive scan of s
+    uint32_t x = s;
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t t = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        wsum[lane] = t;  // inclusive
+    }
+    __syncthreads();
+    uint32_t run = x - s + (w ? wsum[w - 1] : 0);  // exclusive prefix of this thread's chunk
+    for (int k = 0; k < per; k++)
+        if (b0 + k < Tu) {
+            uint32_t t = row[b0 + k];
+            row[b0 + k] = run;
+            run += t;
+        }
+    if (threadIdx.x == 1023) rowsum[blockIdx.x] = run;
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *__restrict__ kin,
+                                                           const uint32_t *__restrict__ vin,
+                                                           uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                           int64_t n, const int64_t *d_n, int shift,
+                                                           const uint32_t *__restrict__ hist, int64_t T,
+                                                           const uint32_t *__restrict__ rowsum)
+{
+    __shared__ uint32_t dbase[256];
+    __shared__ uint32_t wh[RS_WARPS][256];
+    int64_t cnt = count_of(n, d_n);
+    int64_t base = blockIdx.x * (int64_t)SORT_TILE;
+    if (base >= cnt) return;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+
+    // digit bases: exclusive scan of the row totals, plus this tile's row prefix
+    {
+        uint32_t v = rowsum[tid];
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        __shared__ uint32_t ws[RS_WARPS];
+        if (lane == 31) ws[w] = x;
+        __syncthreads();
+        uint32_t off = 0;
+        for (int k = 0; k < w; k++) off += ws[k];
+        dbase[tid] = off + x - v + hist[tid * T + blockIdx.x];
+    }
+#pragma unroll
+    for (int k = 0; k < RS_WARPS; k++) wh[k][tid] = 0;
+    __syncthreads();
+
+    uint64_t kk[RS_ITEMS];
+    uint32_t vv[RS_ITEMS];
+    int dd[RS_ITEMS];
+    const int64_t wbase = base + w * (32 * RS_ITEMS);
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; r++) {
+        int64_t i = wbase + r * 32 + lane;
+        if (i < cnt) { kk[r] = kin[i]; vv[r] = vin[i]; dd[r] = (int)((kk[r] >> shift) & 0xff); }
+        else { kk[r] = 0; vv[r] = 0; dd[r] = 256 + lane; }
+    }
+    // per-warp digit counts
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; r++) {
+        unsigned peers = __match_any_sync(0xffffffffu, dd[r]);
+        if (dd[r] < 256 && (peers & lt) == 0) wh[w][dd[r]] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {  // per-warp bases for digit tid
+        uint32_t run = dbase[tid];
+#pragma unroll
+        for (int k = 0; k < RS_WARPS; k++) {
+            uint32_t t = wh[k][tid];
+            wh[k][tid] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; r++) {
+        unsigned peers = __match_any_sync(0xffffffffu, dd[r]);
+        uint32_t pos = 0;
+        if (dd[r] < 256) pos = wh[w][dd[r]] + __popc(peers & lt);
+        __syncwarp();
+        if (dd[r] < 256 && (peers & lt) == 0) wh[w][dd[r]] += __popc(peers);
+        __syncwarp();
+        if (dd[r] < 256) { kout[pos] = kk[r]; vout[pos] = vv[r]; }
+    }
+}
+
+int radix_sort_pairs(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int64_t n, const int64_t *d_n,
+                     int bits, const SortScratch &s, cudaStream_t st, int64_t *launches)
+{
+    if (n <= 0) return 0;
+    int64_t T = (n + SORT_TILE - 1) / SORT_TILE;
+    int passes = (bits + 7) / 8;
+    uint64_t *ka = k0, *kb = k1;
+    uint32_t *va = v0, *vb = v1;
+    for (int p = 0; p < passes; p++) {
+        int shift = 8 * p;
+        k_rs_hist<<<(unsigned)T, RS_THREADS, 0, st>>>(ka, n, d_n, shift, s.hist, T);
+        k_rs_rowscan<<<256, 1024, 0, st>>>(s.hist, T, d_n, n, s.rowsum);
+        k_rs_scatter<<<(unsigned)T, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, d_n, shift, s.hist, T, s.rowsum);
+        if (launches) *launches += 3;
+        uint64_t *tk = ka; ka = kb; kb = tk;
+        uint32_t *tv = va; va = vb; vb = tv;
+    }
+    return (passes & 1) ? 1 : 0;
+}
+
+}  // namespace hull3d

@@ -1,0 +1,221 @@
+"""Thin ctypes binding of the C ABI in include/hull3d.h.
+
+Argument marshalling only: every step of the hull runs in the CUDA library.
+PyTorch provides device memory and streams.  If the shared library has not
+been built this module raises on first use -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhull3d.so")
+_lock = threading.Lock()
+_lib = None
+
+OK = 0
+ERR_INVALID_ARG = 1
+ERR_COORD_RANGE = 2
+ERR_DUPLICATE = 3
+ERR_CAPACITY = 4
+ERR_OOM = 5
+ERR_BUDGET = 6
+ERR_DEVICE_TIMEOUT = 7
+ERR_CUDA = 8
+ERR_INTERNAL = 9
+
+# every symbol include/hull3d.h declares
+EXPORTS = (
+    "hull3d_plan", "hull3d_destroy", "hull3d_plan_bytes", "hull3d_compute_async", "hull3d_compute",
+    "hull3d_compute_host", "hull3d_batch_async", "hull3d_strerror", "hull3d_last_cuda_error",
+    "hull3d_last_launch_count",
+)
+
+
+class Hull3DError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        lib = load()
+        msg = lib.hull3d_strerror(code).decode()
+        if code == ERR_CUDA:
+            msg += f" (cudaError {lib.hull3d_last_cuda_error()})"
+        super().__init__(f"hull3d{(' ' + what) if what else ''}: {msg}")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("fused_levels", ctypes.c_int32), ("seg_level", ctypes.c_int32), ("seg_events", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+
+def load():
+    """Loads the library (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+            lib = ctypes.CDLL(LIB_PATH)
+            P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+            lib.hull3d_plan.argtypes = [ctypes.POINTER(P), i64, i64, ctypes.POINTER(Opts)]
+            lib.hull3d_plan.restype = ctypes.c_int
+            lib.hull3d_destroy.argtypes = [P]
+            lib.hull3d_destroy.restype = None
+            lib.hull3d_plan_bytes.argtypes = [P]
+            lib.hull3d_plan_bytes.restype = i64
+            lib.hull3d_compute_async.argtypes = [P, P, i64, P, i64, P, P, P]
+            lib.hull3d_compute_async.restype = ctypes.c_int
+            lib.hull3d_compute.argtypes = [P, P, i64, P, i64, ctypes.POINTER(i64), P]
+            lib.hull3d_compute.restype = ctypes.c_int
+            lib.hull3d_compute_host.argtypes = [P, P, i64, P, i64, ctypes.POINTER(i64), P]
+            lib.hull3d_compute_host.restype = ctypes.c_int
+            lib.hull3d_batch_async.argtypes = [P, P, P, i64, P, P, P, P, P]
+            lib.hull3d_batch_async.restype = ctypes.c_int
+            lib.hull3d_strerror.argtypes = [ctypes.c_int]
+            lib.hull3d_strerror.restype = ctypes.c_char_p
+            lib.hull3d_last_cuda_error.argtypes = []
+            lib.hull3d_last_cuda_error.restype = ctypes.c_int
+            lib.hull3d_last_launch_count.argtypes = [P]
+            lib.hull3d_last_launch_count.restype = i64
+            _lib = lib
+    return _lib
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _check_points(xyz, device_needed: bool):
+    import torch
+
+    if not isinstance(xyz, torch.Tensor):
+        raise TypeError("points must be a torch tensor")
+    if xyz.dtype != torch.int32 or xyz.dim() != 2 or xyz.shape[1] != 3:
+        raise ValueError("points must be an (n, 3) int32 tensor")
+    if device_needed and not xyz.is_cuda:
+        raise ValueError("points must be on a CUDA device")
+    return xyz.contiguous()
+
+
+def max_faces(n: int) -> int:
+    return max(2 * n - 4, 0) if n >= 3 else 0
+
+
+class Hull3D:
+    """A plan: scratch for hulls of up to max_n points (and batches totalling max_n)."""
+
+    def __init__(self, max_n: int, max_clouds: int = 0, fused_levels: int = 0, seg_level: int = 0,
+                 seg_events: int = 0, use_graph: int = 0):
+        self._lib = load()
+        opts = Opts(fused_levels, seg_level, seg_events, use_graph)
+        plan = ctypes.c_void_p()
+        rc = self._lib.hull3d_plan(ctypes.byref(plan), int(max_n), int(max_clouds), ctypes.byref(opts))
+        if rc:
+            raise Hull3DError(rc, "plan")
+        self._plan = plan
+        self.max_n = int(max_n)
+
+    def close(self):
+        if getattr(self, "_plan", None):
+            self._lib.hull3d_destroy(self._plan)
+            self._plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def scratch_bytes(self) -> int:
+        return int(self._lib.hull3d_plan_bytes(self._plan))
+
+    @property
+    def last_launches(self) -> int:
+        return int(self._lib.hull3d_last_launch_count(self._plan))
+
+    def compute(self, xyz, stream=None):
+        """Canonical faces (F, 3) int32 on the device of xyz (synchronous)."""
+        import torch
+
+        xyz = _check_points(xyz, True)
+        n = xyz.shape[0]
+        faces = torch.empty((max(max_faces(n), 1), 3), dtype=torch.int32, device=xyz.device)
+        nf = ctypes.c_int64(0)
+        rc = self._lib.hull3d_compute(self._plan, xyz.data_ptr(), n, faces.data_ptr(), max_faces(n), ctypes.byref(nf),
+                                      _stream_ptr(stream))
+        if rc:
+            raise Hull3DError(rc, "compute")
+        return faces[: nf.value]
+
+    def compute_async(self, xyz, faces, d_nfaces=None, d_status=None, stream=None) -> None:
+        """Enqueues the hull; faces is a preallocated (cap, 3) int32 device tensor,
+        d_nfaces an int64 device scalar, d_status an int32 device scalar."""
+        xyz = _check_points(xyz, True)
+        rc = self._lib.hull3d_compute_async(
+            self._plan, xyz.data_ptr(), xyz.shape[0], faces.data_ptr(), faces.shape[0],
+            None if d_nfaces is None else d_nfaces.data_ptr(), None if d_status is None else d_status.data_ptr(),
+            _stream_ptr(stream))
+        if rc:
+            raise Hull3DError(rc, "compute_async")
+
+    def compute_host(self, xyz, faces_out=None, stream=None):
+        """End to end from host memory: xyz is an (n, 3) int32 CPU tensor (pinned
+        for full speed); returns the faces as a CPU tensor view of faces_out."""
+        import torch
+
+        xyz = _check_points(xyz, False)
+        n = xyz.shape[0]
+        if faces_out is None:
+            faces_out = torch.empty((max(max_faces(n), 1), 3), dtype=torch.int32, pin_memory=True)
+        nf = ctypes.c_int64(0)
+        rc = self._lib.hull3d_compute_host(self._plan, xyz.data_ptr(), n, faces_out.data_ptr(), faces_out.shape[0],
+                                           ctypes.byref(nf), _stream_ptr(stream))
+        if rc:
+            raise Hull3DError(rc, "compute_host")
+        return faces_out[: nf.value]
+
+    def batch_async(self, xyz, offsets: np.ndarray, faces, face_offsets: np.ndarray, d_nfaces, d_status,
+                    stream=None) -> None:
+        """Enqueues B hulls; offsets / face_offsets are host int64 arrays of B + 1."""
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        face_offsets = np.ascontiguousarray(face_offsets, dtype=np.int64)
+        B = len(offsets) - 1
+        rc = self._lib.hull3d_batch_async(self._plan, xyz.data_ptr(), offsets.ctypes.data, B, faces.data_ptr(),
+                                          face_offsets.ctypes.data, d_nfaces.data_ptr(), d_status.data_ptr(),
+                                          _stream_ptr(stream))
+        if rc:
+            raise Hull3DError(rc, "batch_async")
+
+    def batch(self, xyz, offsets: np.ndarray, stream=None):
+        """Hulls of B clouds; returns (faces, face_offsets, nfaces, status) with
+        faces on the device and the rest on the host."""
+        import torch
+
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        sizes = np.diff(offsets)
+        caps = np.where(sizes >= 3, 2 * sizes - 4, 0)
+        face_offsets = np.zeros(len(offsets), np.int64)
+        face_offsets[1:] = np.cumsum(caps)
+        dev = xyz.device
+        faces = torch.empty((max(int(face_offsets[-1]), 1), 3), dtype=torch.int32, device=dev)
+        nf = torch.zeros(len(sizes), dtype=torch.int64, device=dev)
+        st = torch.zeros(len(sizes), dtype=torch.int32, device=dev)
+        self.batch_async(xyz, offsets, faces, face_offsets, nf, st, stream)
+        return faces, face_offsets, nf.cpu().numpy(), st.cpu().numpy()
+
+
+def hull(xyz, **kw):
+    """One-shot convenience: canonical faces of the (n, 3) int32 CUDA tensor xyz."""
+    h = Hull3D(max(int(xyz.shape[0]), 4), **kw)
+    try:
+        return h.compute(xyz)
+    finally:
+        h.close()

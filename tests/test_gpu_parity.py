@@ -1,0 +1,170 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the CPU oracle.
+
+The bar is bit-exactness of the canonical face lists (integer output)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1205_1171_gb300 import inputs
+from tests import validators as V
+from tests.test_oracle_hull import _tiny_sets
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1205_1171_gb300 import build, hull3d
+
+    build.build()
+    hull3d.load()
+    return hull3d
+
+
+@pytest.fixture(scope="module")
+def plan(H):
+    p = H.Hull3D(1 << 17)
+    yield p
+    p.close()
+
+
+def run(plan, pts):
+    return plan.compute(torch.from_numpy(np.ascontiguousarray(pts, dtype=np.int32)).cuda()).cpu().numpy()
+
+
+def test_tiny_degenerate_sets(plan):
+    for pts in _tiny_sets(400, 11):
+        assert np.array_equal(run(plan, pts), oracle.hull(pts)), pts.tolist()
+
+
+def test_ragged_sizes_all_distributions(plan):
+    sizes = [1, 2, 3, 4, 5, 6, 7, 8, 9, 15, 16, 17, 31, 33, 63, 64, 65, 127, 129, 255, 256, 257, 511, 513, 1000,
+             1023, 1024, 1025, 2049, 4095, 4097, 10000]
+    for dist in inputs.DISTS:
+        for n in sizes:
+            pts = inputs.cloud_seeded(dist, n, 500 + n)
+            got = run(plan, pts)
+            assert np.array_equal(got, oracle.hull(pts)), (dist, n)
+
+
+@pytest.mark.parametrize("fused", [1, 2, 3, 5, 7, 9, 10])
+def test_fused_depths_agree(H, fused):
+    p = H.Hull3D(1 << 14, fused_levels=fused)
+    try:
+        for dist in inputs.DISTS:
+            for n in (300, 3001, 1 << 14):
+                pts = inputs.cloud_seeded(dist, n, 900 + n + fused)
+                assert np.array_equal(run(p, pts), oracle.hull(pts)), (dist, n, fused)
+    finally:
+        p.close()
+
+
+def test_config_small_cube_4096(plan):
+    pts = inputs.cloud_seeded("cube", 4096, inputs.seed_for(1))
+    got = run(plan, pts)
+    assert np.array_equal(got, oracle.hull(pts))
+    V.check_all(pts, got)
+
+
+@pytest.mark.parametrize("dist", inputs.DISTS)
+def test_2e16_all_distributions(plan, dist):
+    pts = inputs.cloud_seeded(dist, 1 << 16, 77)
+    got = run(plan, pts)
+    assert np.array_equal(got, oracle.hull(pts))
+
+
+def test_degenerate_structured(plan):
+    rng = np.random.default_rng(3)
+    # a full 3D grid: every kind of degeneracy
+    g = np.array(np.meshgrid(*[np.arange(-6, 7)] * 3)).reshape(3, -1).T * 1000
+    cases = [g, rng.permutation(g)]
+    # cube corners + faces + edges + interior
+    c = rng.integers(-5, 6, size=(3000, 3))
+    ax = rng.integers(0, 3, size=3000)
+    c[np.arange(3000), ax] = rng.choice([-5, 5], size=3000)
+    cases.append(np.unique(c, axis=0))
+    # points on a few vertical lines and coplanar slabs, wide coordinates
+    lines = np.concatenate([np.stack([np.full(50, x), np.full(50, y), np.arange(50) * 9973], 1)
+                            for x, y in [(0, 0), (1 << 19, 3), (-(1 << 19), -7)]])
+    cases.append(lines)
+    # cyclic polytope (general position, all points on the hull)
+    t = np.arange(-101, 102)
+    cases.append(np.stack([t, t**2, t**3], 1))
+    # extreme magnitudes
+    e = np.array([[x, y, z] for x in (-(1 << 20), (1 << 20) - 1) for y in (-(1 << 20), 0, (1 << 20) - 1)
+                  for z in (-(1 << 20), (1 << 20) - 1)])
+    cases.append(e)
+    for pts in cases:
+        pts = pts.astype(np.int32)
+        assert np.array_equal(run(plan, pts), oracle.hull(pts))
+
+
+def test_errors_are_reported(H, plan):
+    bad = np.array([[0, 0, 1 << 20], [1, 2, 3], [4, 5, 6], [7, 8, 9]], np.int32)
+    with pytest.raises(H.Hull3DError) as e:
+        run(plan, bad)
+    assert e.value.code == H.ERR_COORD_RANGE
+    dup = np.array([[1, 2, 3], [4, 5, 6], [1, 2, 3], [0, 0, 0]], np.int32)
+    with pytest.raises(H.Hull3DError) as e:
+        run(plan, dup)
+    assert e.value.code == H.ERR_DUPLICATE
+    # a plan keeps working after an error
+    ok = inputs.cloud_seeded("ball", 500, 1)
+    assert np.array_equal(run(plan, ok), oracle.hull(ok))
+    # capacity and size limits are host-side errors
+    xyz = torch.from_numpy(ok).cuda()
+    small = torch.empty((10, 3), dtype=torch.int32, device="cuda")
+    with pytest.raises(H.Hull3DError) as e:
+        plan.compute_async(xyz, small)
+    assert e.value.code == H.ERR_CAPACITY
+    big = H.Hull3D(100)
+    with pytest.raises(H.Hull3DError) as e:
+        big.compute(xyz)
+    assert e.value.code == H.ERR_INVALID_ARG
+    big.close()
+
+
+def test_async_form_and_status(H, plan):
+    pts = inputs.cloud_seeded("sphere", 3000, 5)
+    xyz = torch.from_numpy(pts).cuda()
+    faces = torch.empty((2 * 3000 - 4, 3), dtype=torch.int32, device="cuda")
+    nf = torch.zeros(1, dtype=torch.int64, device="cuda")
+    st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    plan.compute_async(xyz, faces, nf, st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    got = faces[: int(nf.item())].cpu().numpy()
+    assert np.array_equal(got, oracle.hull(pts))
+
+
+def test_host_buffers_end_to_end(plan):
+    pts = inputs.cloud_seeded("gauss", 20000, 8)
+    got = plan.compute_host(torch.from_numpy(pts).pin_memory()).numpy()
+    assert np.array_equal(got, oracle.hull(pts))
+
+
+def test_batch_matches_single(H):
+    xyz, off, kinds = inputs.batch(40, 12, 4.0, 10.0)
+    p = H.Hull3D(len(xyz), max_clouds=40)
+    faces, foff, nf, st = p.batch(torch.from_numpy(xyz).cuda(), off)
+    torch.cuda.synchronize()
+    f = faces.cpu().numpy()
+    for b in range(40):
+        assert st[b] == 0
+        got = f[foff[b]: foff[b] + nf[b]]
+        assert np.array_equal(got, oracle.hull(xyz[off[b]: off[b + 1]])), b
+    p.close()
+
+
+@pytest.mark.parametrize("dist", ["ball", "sphere"])
+def test_2e20_bit_exact(H, dist):
+    """The 2^20-point configurations (ball: few hull points; sphere: ~2n faces)."""
+    pts = inputs.cloud_seeded(dist, 1 << 20, inputs.seed_for(2))
+    p = H.Hull3D(1 << 20)
+    got = p.compute(torch.from_numpy(pts).cuda()).cpu().numpy()
+    p.close()
+    want = oracle.hull(pts)
+    assert np.array_equal(got, want)
