@@ -1,6 +1,7 @@
 // api.cu -- the C ABI: plan (all scratch allocated up front), the level driver
 // (the paper's host "main outer loop", Sec. 3, replayed without host syncs)
 // and the entry points declared in include/hull3d.h.
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -24,6 +25,36 @@ int cuda_fail(cudaError_t e)
     do {                                           \
         cudaError_t e_ = (call);                   \
         if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+
+// HULL3D_DEBUG_SYNC=1: synchronise after every step and name the failing one
+// on stderr (a diagnostic mode; the default path never synchronises or prints).
+bool debug_sync()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("HULL3D_DEBUG_SYNC");
+        v = (e && *e && *e != '0') ? 1 : 0;
+    }
+    return v == 1;
+}
+
+int step_check(cudaStream_t st, const char *what)
+{
+    if (!debug_sync()) return HULL3D_OK;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        fprintf(stderr, "hull3d: step '%s' failed: %s\n", what, cudaGetErrorString(e));
+        return cuda_fail(e);
+    }
+    return HULL3D_OK;
+}
+
+#define STEP(what)                                  \
+    do {                                            \
+        int rc_ = step_check(st, what);             \
+        if (rc_) return rc_;                        \
     } while (0)
 
 int ceil_log2(int64_t n)
@@ -113,12 +144,16 @@ int enqueue_hull(hull3d_plan_s *p, const int32_t *d_xyz, int64_t n, int32_t *d_f
                  cudaStream_t st)
 {
     int64_t launches = 0;
+    STEP("entry");
     CK(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
     launch_keys(d_xyz, n, p->k0, p->v0, status, st);
     launches++;
+    STEP("keys");
     int which = radix_sort_pairs(p->k0, p->v0, p->k1, p->v1, n, nullptr, 63, p->ss, st, &launches);
+    STEP("point sort");
     launch_decode(which ? p->k1 : p->k0, which ? p->v1 : p->v0, n, p->X, p->Y, p->Z, p->ID, status, st);
     launches++;
+    STEP("decode");
     if (n < 3) {
         CK(cudaMemsetAsync(nf, 0, sizeof(int64_t), st));
         p->last_launches = launches;
@@ -131,18 +166,23 @@ int enqueue_hull(hull3d_plan_s *p, const int32_t *d_xyz, int64_t n, int32_t *d_f
     if (l1 > 10) l1 = 10;
     launch_fused(pts, n, 0, l1, p->pass, 2, status, st);
     launches++;
+    STEP("fused levels");
     for (int level = l1 + 1; level <= L; level++) {
         launch_level(pts, n, level, p->pass, 2, status, st);
         int64_t last_lo = (((n + (1ll << level) - 1) >> level) - 1) << level;
         launches += (last_lo + (1ll << (level - 1)) >= n) ? 2 : 1;  // level + pass-through copy
+        STEP("merge level");
     }
     int fbits = ceil_log2(n);
     if (fbits < 1) fbits = 1;
     launch_face_keys(pts, n, L, p->pass, p->k0, p->v0, nf, status, st);
     launches++;
+    STEP("face keys");
     which = radix_sort_pairs(p->k0, p->v0, p->k1, p->v1, 2 * n, nf, 2 * fbits, p->ss, st, &launches);
+    STEP("face sort");
     launch_face_out(which ? p->k1 : p->k0, which ? p->v1 : p->v0, 2 * n, fbits, nf, d_faces, st);
     launches++;
+    STEP("face out");
     p->last_launches = launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);

@@ -200,10 +200,11 @@ void launch_fused(const Points &pts, int64_t n, int l0, int l1, PassBufs *passes
     (void)l0;
     int64_t blocks = (n + (1ll << l1) - 1) >> l1;
     size_t smem = fused_smem_bytes(l1);
-    static bool attr_set[16] = {};
-    if (!attr_set[l1]) {
-        cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_set[l1] = true;
+    // the attribute is per kernel: raise it once to the largest depth's need
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem_bytes(10));
+        attr_set = true;
     }
     k_fused<<<(unsigned)blocks, FUSED_THREADS, smem, st>>>(pts, n, l1, passes[0], passes[npass - 1], npass, status);
 }
