@@ -1,0 +1,301 @@
+"""Benchmark of the GB300 kinetic divide-and-conquer 3D hull.
+
+One step = the whole hot path (range check, radix sort, every merge level of
+both passes, face emission and canonical sort) over the two n = 2^24 clouds of
+the headline workload: uniform in the cube [-2^20, 2^20)^3 and an isotropic
+Gaussian (sigma = 2^18) clipped to the cube.  Points are already resident in
+HBM when the timed region starts (each cloud is 201 MB, above the 129 MB L2).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the plain serial implementation the
+CUDA path is checked against) on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpoints/s per hull at n=2^24 and hulls/s batched (bit-exact), % of HBM roofline"
+UNIT = "Mpoints/s"
+N_POINTS = 1 << 24
+DISTS = ("cube", "gauss")
+WORKLOAD = "single hulls at n=2^24: uniform cube + isotropic Gaussian sigma=2^18 clipped to the cube (one of each per step)"
+ORACLE_SAMPLE = 1 << 17  # points per cloud in one step of the reference arm
+BASELINE_SAMPLE = 1 << 19  # points per cloud in the cpu_baseline leg
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def make_inputs(rank: int, n: int = N_POINTS):
+    from paper_1205_1171_gb300 import inputs
+
+    return [inputs.cloud_seeded(d, n, inputs.seed_for(30 + i) + 1000 * rank) for i, d in enumerate(DISTS)]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def alg_bytes(n: int, ev: np.ndarray, fused_l1: int, nfaces: int) -> dict:
+    """Algorithmic bytes per call and phase (the definitions are in the design doc)."""
+    L = int(np.ceil(np.log2(n)))
+    l1 = min(fused_l1, L)
+    out = {"sort": 28 * n, "fused": 16 * n, "levels": 0, "seg": 0, "faces": 72 * nfaces}
+    for p in range(2):
+        out["fused"] += 8 * n + 12 * int(ev[p, l1])
+        for lv in range(l1 + 1, L + 1):
+            out["levels"] += 20 * int(ev[p, lv - 1]) + 12 * int(ev[p, lv])
+    return out
+
+
+def run_reference(args, rank: int, world: int):
+    """The CPU oracle, as it stands, on bounded samples of the same workload."""
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    clouds = make_inputs(0)
+    samples = [c[:ORACLE_SAMPLE].copy() for c in clouds]
+    for _ in range(args.warmup):
+        for s in samples:
+            oracle.hull(s)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for s in samples:
+            oracle.hull(s)
+    dt = time.perf_counter() - t0
+    value = len(samples) * ORACLE_SAMPLE * args.steps / dt / 1e6
+    sample = f"first {ORACLE_SAMPLE} points of each of the two n=2^24 clouds per step (single-threaded C oracle)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N_POINTS, "sample_points_per_cloud": ORACLE_SAMPLE},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_leg():
+    import oracle
+
+    oracle.build()
+    clouds = make_inputs(0)
+    s = BASELINE_SAMPLE
+    samples = [c[:s].copy() for c in clouds]
+    t0 = time.perf_counter()
+    for x in samples:
+        oracle.hull(x)
+    dt = time.perf_counter() - t0
+    return {"value": len(samples) * s / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {s} points of each of the two n=2^24 clouds, once (single-threaded C oracle)",
+            "seconds": dt}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fused", type=int, default=0, help="fused bottom levels (0 = library default)")
+    ap.add_argument("--occ", type=int, default=0, help="global merge kernel occupancy knob (1 or 4)")
+    ap.add_argument("--cmp-level", type=int, default=0, help="first level of the compacted warp kernel (0 = default)")
+    ap.add_argument("--n", type=int, default=1 << 24, help="points per cloud (profiling runs only; default 2^24)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    npts = args.n
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    from paper_1205_1171_gb300 import build, hull3d
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    clouds = make_inputs(rank, npts)
+    dev_clouds = [torch.from_numpy(c).cuda() for c in clouds]
+    plan = hull3d.Hull3D(npts, fused_levels=args.fused, level_occupancy=args.occ, cmp_level=args.cmp_level)
+    cap = 2 * npts - 4
+    faces = [torch.empty((cap, 3), dtype=torch.int32, device="cuda") for _ in clouds]
+    nfs = [torch.zeros(1, dtype=torch.int64, device="cuda") for _ in clouds]
+    sts = [torch.zeros(1, dtype=torch.int32, device="cuda") for _ in clouds]
+    stream = torch.cuda.current_stream()
+
+    def step():
+        launches = 0
+        for x, f, nf, st in zip(dev_clouds, faces, nfs, sts):
+            plan.compute_async(x, f, nf, st, stream)
+            launches += plan.last_launches
+        return launches
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for st in sts:
+        assert int(st.item()) == 0, "device status"
+    nface = [int(nf.item()) for nf in nfs]
+    level_ev = []
+    for x in dev_clouds:  # per-level movie lengths of each cloud (statistics for the roofline)
+        plan.compute_async(x, faces[0], nfs[0], sts[0], stream)
+        level_ev.append(plan.level_events())
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    plan.profile(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        launches += step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    clk = clocks.stop()
+    phase_ms, calls = plan.profile_read()
+    plan.profile(False)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    points = len(clouds) * npts * args.steps * world
+    value = points / (ms / 1e3) / 1e6
+
+    # end to end through the public API from pinned host memory
+    host_in = [torch.from_numpy(c).pin_memory() for c in clouds]
+    host_out = torch.empty((cap, 3), dtype=torch.int32).pin_memory()
+    for x in host_in:
+        plan.compute_host(x, host_out)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    d2h = 0
+    for _ in range(args.steps):
+        for x in host_in:
+            f = plan.compute_host(x, host_out)
+            d2h += f.shape[0] * 12 + 12
+    e_dt = time.perf_counter() - e0
+    if dist:
+        t = torch.tensor([e_dt], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e_dt = float(t.item())
+    e2e = {"value": points / e_dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": 12 * npts * len(clouds),
+           "d2h_bytes_per_step": d2h // args.steps}
+
+    # roofline of the dominant phase, from the phase events recorded live in the timed region
+    peak, peak_kind = peaks()
+    ab = [alg_bytes(npts, ev, plan.fused_levels_used, nf) for ev, nf in zip(level_ev, nface)]
+    alg = {k: sum(a[k] for a in ab) for k in ab[0]}  # bytes per step
+    dom = max(phase_ms, key=lambda k: phase_ms[k])
+    per_step_ms = phase_ms[dom] / max(args.steps, 1)
+    achieved = alg[dom] / (per_step_ms / 1e3) / 1e9 if per_step_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "phase": dom, "peak_kind": peak_kind,
+                "phase_ms_per_step": {k: v / max(args.steps, 1) for k, v in phase_ms.items()},
+                "alg_bytes_per_step": alg}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": npts, "clouds_per_step": len(clouds),
+                       "faces": nface, "l2": "inputs larger than L2 (201 MB per cloud), no flush",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_leg()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -60,7 +60,10 @@ typedef struct {
     int32_t seg_level;      /* first level merged time-segment-parallel; < 0 disables */
     int32_t seg_events;     /* target child events per time segment */
     int32_t use_graph;      /* 1: replay the level sequence as a CUDA graph (default), -1: plain launches */
-    int32_t reserved[4];
+    int32_t level_occupancy; /* global merge kernel: 1 = no register cap, 4 = at most 128 registers (4 CTAs/SM) */
+    int32_t cmp_level;      /* first level merged by the compacted warp-per-merge kernel */
+    int32_t cmp_slots;      /* its shared-memory table size in points (<= 4096) */
+    int32_t reserved[1];
 } hull3d_opts;
 
 /* Creates a plan for hulls of up to max_n points (hull3d_compute*) and for
@@ -69,6 +72,9 @@ typedef struct {
  * device.  opts may be NULL.  On failure *out is NULL and the code is
  * HULL3D_ERR_INVALID_ARG or HULL3D_ERR_OOM. */
 int hull3d_plan(hull3d_plan_t *out, int64_t max_n, int64_t max_clouds, const hull3d_opts *opts);
+
+/* Copies the plan's effective options (automatic fields resolved) into *out. */
+int hull3d_plan_opts(hull3d_plan_t plan, hull3d_opts *out);
 
 /* Frees the plan and its scratch (synchronises the device first). NULL is a no-op. */
 void hull3d_destroy(hull3d_plan_t plan);
@@ -124,6 +130,30 @@ int hull3d_last_cuda_error(void);
 /* Number of kernel launches the last call on this plan enqueued (graph nodes
  * count one each). */
 int64_t hull3d_last_launch_count(hull3d_plan_t plan);
+
+/* Phase timing.  With enable = 1, every later single-hull call records CUDA
+ * events on its own stream at the boundaries of its phases
+ *   0 sort   (range check, key build, radix sort, decode, duplicate check)
+ *   1 fused  (bottom merge levels in shared memory)
+ *   2 levels (merge levels in global memory)
+ *   3 seg    (time-segment-parallel top levels)
+ *   4 faces  (face emission and canonical sort)
+ * hull3d_profile_read waits for the recorded events, writes the per-phase
+ * milliseconds summed over the recorded calls into ms[HULL3D_PHASES] and the
+ * number of calls into *calls, and clears the record.  enable = 0 stops
+ * recording. */
+#define HULL3D_PHASES 5
+int hull3d_profile(hull3d_plan_t plan, int enable);
+int hull3d_profile_read(hull3d_plan_t plan, double *ms, int64_t *calls);
+
+/* Per merge level launched in global memory: ms[level] summed over the
+ * recorded calls (call before hull3d_profile_read, which clears the record). */
+int hull3d_profile_levels(hull3d_plan_t plan, double *ms);
+
+/* Movie lengths of the last single-hull call: out[pass * 64 + level] is the
+ * total number of events written at that merge level (pass 0 lower, 1
+ * upper).  Synchronises the device. */
+int hull3d_level_events(hull3d_plan_t plan, int64_t *out);
 
 #ifdef __cplusplus
 }

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "internal.h"
 
@@ -77,7 +78,7 @@ struct hull3d_plan_s {
     uint32_t *v0 = nullptr, *v1 = nullptr;
     SortScratch ss{};
     // rank-ordered points
-    int32_t *X = nullptr, *Y = nullptr, *Z = nullptr, *ID = nullptr;
+    int4 *P4 = nullptr;
     PassBufs pass[2]{};
     int32_t *status = nullptr;
     int64_t *nfaces = nullptr;
@@ -86,6 +87,13 @@ struct hull3d_plan_s {
     int64_t *h_nfaces = nullptr;
     int32_t *h_status = nullptr;
     int64_t last_launches = 0;
+    unsigned long long *lev_stats = nullptr;  // [2][64]
+    // phase profiling
+    bool profile = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<int> marks;  // per recorded call: HULL3D_PHASES + 1 event indices
+    std::vector<int> level_marks;  // per recorded level launch: (level, start event, end event)
 };
 
 namespace {
@@ -115,10 +123,7 @@ size_t layout(hull3d_plan_s *p, char *base)
     p->ss.max_tiles = (N2 + SORT_TILE - 1) / SORT_TILE;
     p->ss.hist = b.take<uint32_t>(256 * p->ss.max_tiles);
     p->ss.rowsum = b.take<uint32_t>(256);
-    p->X = b.take<int32_t>(N);
-    p->Y = b.take<int32_t>(N);
-    p->Z = b.take<int32_t>(N);
-    p->ID = b.take<int32_t>(N);
+    p->P4 = b.take<int4>(N);
     for (int s = 0; s < 2; s++) {
         PassBufs &pb = p->pass[s];
         for (int k = 0; k < 2; k++) {
@@ -127,9 +132,12 @@ size_t layout(hull3d_plan_s *p, char *base)
             pb.B[k] = b.take<int32_t>(N2);
             pb.cnt[k] = b.take<int32_t>(N);
         }
-        pb.prv = b.take<int32_t>(N);
-        pb.nxt = b.take<int32_t>(N);
+        pb.lk = b.take<int2>(N);
+        pb.gmap = b.take<int32_t>(N);
     }
+    p->lev_stats = b.take<unsigned long long>(128);
+    p->pass[0].lev_events = p->lev_stats;
+    p->pass[1].lev_events = p->lev_stats + 64;
     p->status = b.take<int32_t>(1);
     p->nfaces = b.take<int64_t>(1);
     p->stage_xyz = b.take<int32_t>(3 * N);
@@ -137,42 +145,93 @@ size_t layout(hull3d_plan_s *p, char *base)
     return b.off;
 }
 
-int default_fused(const hull3d_plan_s *p) { return p->opts.fused_levels > 0 ? p->opts.fused_levels : 8; }
+// Defaults from the measured level sweep (2^24 cube and clipped Gaussian, GB300):
+// no fused bottom kernel, the 128-register thread-per-merge kernel up to level
+// 9, the uncapped one for levels 10-12, the compacted warp kernel from 13 on.
+int default_fused(const hull3d_plan_s *p) { return p->opts.fused_levels > 0 ? p->opts.fused_levels : 1; }
+int default_occupancy(const hull3d_plan_s *p, int level)
+{
+    if (p->opts.level_occupancy > 0) return p->opts.level_occupancy;
+    return level <= 9 ? 4 : 1;
+}
+int default_cmp_level(const hull3d_plan_s *p) { return p->opts.cmp_level > 0 ? p->opts.cmp_level : 13; }
+int default_cmp_slots(const hull3d_plan_s *p) { return p->opts.cmp_slots > 0 ? p->opts.cmp_slots : 1024; }
+
+// Records a phase-boundary event when profiling (one per boundary per call).
+int mark(hull3d_plan_s *p, cudaStream_t st, int *slot)
+{
+    if (!p->profile) return HULL3D_OK;
+    if (p->ev_used == p->ev_pool.size()) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        p->ev_pool.push_back(e);
+    }
+    *slot = (int)p->ev_used++;
+    CK(cudaEventRecord(p->ev_pool[*slot], st));
+    return HULL3D_OK;
+}
+
+#define MARK(k)                                      \
+    do {                                             \
+        int rc_ = mark(p, st, &slots[k]);            \
+        if (rc_) return rc_;                         \
+    } while (0)
 
 // Enqueues the whole single-hull pipeline.
 int enqueue_hull(hull3d_plan_s *p, const int32_t *d_xyz, int64_t n, int32_t *d_faces, int64_t *nf, int32_t *status,
                  cudaStream_t st)
 {
     int64_t launches = 0;
+    int slots[HULL3D_PHASES + 1];
     STEP("entry");
+    MARK(0);
     CK(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
+    CK(cudaMemsetAsync(p->lev_stats, 0, 128 * sizeof(unsigned long long), st));
     launch_keys(d_xyz, n, p->k0, p->v0, status, st);
     launches++;
     STEP("keys");
     int which = radix_sort_pairs(p->k0, p->v0, p->k1, p->v1, n, nullptr, 63, p->ss, st, &launches);
     STEP("point sort");
-    launch_decode(which ? p->k1 : p->k0, which ? p->v1 : p->v0, n, p->X, p->Y, p->Z, p->ID, status, st);
+    launch_decode(which ? p->k1 : p->k0, which ? p->v1 : p->v0, n, p->P4, status, st);
     launches++;
     STEP("decode");
+    MARK(1);
     if (n < 3) {
         CK(cudaMemsetAsync(nf, 0, sizeof(int64_t), st));
+        for (int k = 2; k <= HULL3D_PHASES; k++) MARK(k);
+        if (p->profile) p->marks.insert(p->marks.end(), slots, slots + HULL3D_PHASES + 1);
         p->last_launches = launches;
-        return cudaGetLastError() == cudaSuccess ? HULL3D_OK : HULL3D_ERR_CUDA;
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? HULL3D_OK : cuda_fail(e);
     }
-    Points pts{ p->X, p->Y, p->Z, p->ID };
+    Points pts{ p->P4 };
     const int L = ceil_log2(n);
     int l1 = default_fused(p);
     if (l1 > L) l1 = L;
     if (l1 > 10) l1 = 10;
-    launch_fused(pts, n, 0, l1, p->pass, 2, status, st);
+    if (l1 <= 1) launch_level1(n, p->pass, 2, status, st);  // pairs need no merge
+    else launch_fused(pts, n, 0, l1, p->pass, 2, status, st);
     launches++;
     STEP("fused levels");
+    MARK(2);
     for (int level = l1 + 1; level <= L; level++) {
-        launch_level(pts, n, level, p->pass, 2, status, st);
+        int lv0 = -1, lv1 = -1;
+        if (p->profile) { int r_ = mark(p, st, &lv0); if (r_) return r_; }
+        if (level >= default_cmp_level(p))
+            launch_level_cmp(pts, n, level, p->pass, 2, status, st, default_cmp_slots(p));
+        else
+            launch_level(pts, n, level, p->pass, 2, status, st, default_occupancy(p, level));
+        if (p->profile) {
+            int r_ = mark(p, st, &lv1);
+            if (r_) return r_;
+            p->level_marks.insert(p->level_marks.end(), { level, lv0, lv1 });
+        }
         int64_t last_lo = (((n + (1ll << level) - 1) >> level) - 1) << level;
         launches += (last_lo + (1ll << (level - 1)) >= n) ? 2 : 1;  // level + pass-through copy
         STEP("merge level");
     }
+    MARK(3);
+    MARK(4);
     int fbits = ceil_log2(n);
     if (fbits < 1) fbits = 1;
     launch_face_keys(pts, n, L, p->pass, p->k0, p->v0, nf, status, st);
@@ -183,6 +242,8 @@ int enqueue_hull(hull3d_plan_s *p, const int32_t *d_xyz, int64_t n, int32_t *d_f
     launch_face_out(which ? p->k1 : p->k0, which ? p->v1 : p->v0, 2 * n, fbits, nf, d_faces, st);
     launches++;
     STEP("face out");
+    MARK(5);
+    if (p->profile) p->marks.insert(p->marks.end(), slots, slots + HULL3D_PHASES + 1);
     p->last_launches = launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
@@ -213,7 +274,10 @@ int hull3d_plan(hull3d_plan_t *out, int64_t max_n, int64_t max_clouds, const hul
     p->max_n = max_n < 4 ? 4 : max_n;
     p->max_clouds = max_clouds;
     if (opts) p->opts = *opts;
-    if (p->opts.fused_levels < 0 || p->opts.fused_levels > 10) { delete p; return HULL3D_ERR_INVALID_ARG; }
+    if (p->opts.fused_levels < 0 || p->opts.fused_levels > 10 || p->opts.cmp_slots < 0 || p->opts.cmp_slots > 4096) {
+        delete p;
+        return HULL3D_ERR_INVALID_ARG;
+    }
     cudaGetDevice(&p->device);
     p->pool_bytes = layout(p, nullptr);
     cudaError_t e = cudaMalloc((void **)&p->pool, p->pool_bytes);
@@ -239,12 +303,24 @@ void hull3d_destroy(hull3d_plan_t p)
 {
     if (!p) return;
     cudaDeviceSynchronize();
+    for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
     cudaFree(p->pool);
     cudaFreeHost(p->h_nfaces);
     delete p;
 }
 
 int64_t hull3d_plan_bytes(hull3d_plan_t p) { return p ? (int64_t)p->pool_bytes : 0; }
+
+int hull3d_plan_opts(hull3d_plan_t p, hull3d_opts *out)
+{
+    if (!p || !out) return HULL3D_ERR_INVALID_ARG;
+    *out = p->opts;
+    out->fused_levels = default_fused(p);
+    out->level_occupancy = p->opts.level_occupancy;
+    out->cmp_level = default_cmp_level(p);
+    out->cmp_slots = default_cmp_slots(p);
+    return HULL3D_OK;
+}
 
 int64_t hull3d_last_launch_count(hull3d_plan_t p) { return p ? p->last_launches : 0; }
 
@@ -316,6 +392,59 @@ int hull3d_batch_async(hull3d_plan_t p, const int32_t *d_xyz, const int64_t *h_o
         launches += p->last_launches;
     }
     p->last_launches = launches;
+    return HULL3D_OK;
+}
+
+int hull3d_profile(hull3d_plan_t p, int enable)
+{
+    if (!p) return HULL3D_ERR_INVALID_ARG;
+    p->profile = enable != 0;
+    p->marks.clear();
+    p->level_marks.clear();
+    p->ev_used = 0;
+    return HULL3D_OK;
+}
+
+int hull3d_profile_levels(hull3d_plan_t p, double *ms)
+{
+    if (!p || !ms) return HULL3D_ERR_INVALID_ARG;
+    for (int k = 0; k < 64; k++) ms[k] = 0.0;
+    if (!p->level_marks.empty()) CK(cudaEventSynchronize(p->ev_pool[p->level_marks.back()]));
+    for (size_t i = 0; i + 3 <= p->level_marks.size(); i += 3) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, p->ev_pool[p->level_marks[i + 1]], p->ev_pool[p->level_marks[i + 2]]));
+        ms[p->level_marks[i] & 63] += t;
+    }
+    return HULL3D_OK;
+}
+
+int hull3d_profile_read(hull3d_plan_t p, double *ms, int64_t *calls)
+{
+    if (!p || !ms) return HULL3D_ERR_INVALID_ARG;
+    for (int k = 0; k < HULL3D_PHASES; k++) ms[k] = 0.0;
+    const int per = HULL3D_PHASES + 1;
+    int64_t nc = (int64_t)(p->marks.size() / per);
+    if (nc > 0) CK(cudaEventSynchronize(p->ev_pool[p->marks.back()]));
+    for (int64_t c = 0; c < nc; c++)
+        for (int k = 0; k < HULL3D_PHASES; k++) {
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, p->ev_pool[p->marks[c * per + k]], p->ev_pool[p->marks[c * per + k + 1]]));
+            ms[k] += t;
+        }
+    if (calls) *calls = nc;
+    p->marks.clear();
+    p->level_marks.clear();
+    p->ev_used = 0;
+    return HULL3D_OK;
+}
+
+int hull3d_level_events(hull3d_plan_t p, int64_t *out)
+{
+    if (!p || !out) return HULL3D_ERR_INVALID_ARG;
+    unsigned long long tmp[128];
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(tmp, p->lev_stats, sizeof tmp, cudaMemcpyDeviceToHost));
+    for (int k = 0; k < 128; k++) out[k] = (int64_t)tmp[k];
     return HULL3D_OK;
 }
 

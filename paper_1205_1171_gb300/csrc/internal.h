@@ -25,20 +25,22 @@ int radix_sort_pairs(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int
 // A1: range check and key build: key = (x + 2^20) << 42 | (z + 2^20) << 21 | (y + 2^20).
 void launch_keys(const int32_t *xyz, int64_t n, uint64_t *keys, uint32_t *vals, int32_t *status, cudaStream_t st);
 
-// After the sort: decode the sorted keys to the rank-ordered SoA and flag duplicates.
-void launch_decode(const uint64_t *keys, const uint32_t *vals, int64_t n, int32_t *X, int32_t *Y, int32_t *Z,
-                   int32_t *ID, int32_t *status, cudaStream_t st);
+// After the sort: decode the sorted keys to rank-ordered points (x, y, z, input
+// index) and flag duplicates.
+void launch_decode(const uint64_t *keys, const uint32_t *vals, int64_t n, int4 *P, int32_t *status, cudaStream_t st);
 
 // Event-list storage of one pass: two ping-pong buffers (W with the insert flag, A, B) and counts by node lo.
 struct PassBufs {
     unsigned *W[2];
     int32_t *A[2], *B[2];
     int32_t *cnt[2];
-    int32_t *prv, *nxt;
+    int2 *lk;                        // [n]: (prev, next) ranks, NIL = -1
+    unsigned long long *lev_events;  // [64]: events written per level (statistics)
+    int32_t *gmap;                   // [n]: rank -> slot scratch of the compacted merge
 };
 
 struct Points {
-    const int32_t *X, *Y, *Z, *ID;
+    const int4 *P;  // [n]: (x, y, z, input index) by rank
 };
 
 // Level 1 (pairs) for both passes: links of each pair, empty movies.
@@ -50,7 +52,12 @@ void launch_fused(const Points &pts, int64_t n, int l0, int l1, PassBufs *passes
 
 // One level (>= 2), one thread per merge, global memory.
 void launch_level(const Points &pts, int64_t n, int level, PassBufs *passes, int npass, int32_t *status,
-                  cudaStream_t st);
+                  cudaStream_t st, int occupancy);
+
+// One level (>= 2), one warp per merge on a compacted shared-memory table of
+// up to scap slots (merges that do not fit run the global-memory merge).
+void launch_level_cmp(const Points &pts, int64_t n, int level, PassBufs *passes, int npass, int32_t *status,
+                      cudaStream_t st, int scap);
 
 // Faces of the root movies of both passes (level L = ceil(log2 n) in buffer L & 1):
 // orient, rotate min-first, build the sort key (f0 << 28 | f1) and value f2.

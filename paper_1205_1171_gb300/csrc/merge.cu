@@ -2,7 +2,7 @@
 // Sec. 3 main loop and kernel index math) and the face emission.
 //
 // Layout (one pass; the lower and upper passes have separate copies):
-//   links prv/nxt[rank]                      in-place, as in the paper's P[].prev/next
+//   links lk[rank] = (prev, next)            in-place, as in the paper's P[].prev/next
 //   event buffers W/A/B[2][2n]               ping-pong per level (the paper's A and B)
 //   counts cnt[2][n]                         movie length, indexed by the node's first rank
 // The node of level l with first rank lo covers [lo, min(lo + 2^l, n)); its
@@ -24,14 +24,13 @@ __global__ void k_level1(int64_t n, PassBufs p0, PassBufs p1, int32_t *status)
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n) return;
     const bool up = blockIdx.y != 0;
-    int *prv = up ? p1.prv : p0.prv, *nxt = up ? p1.nxt : p0.nxt, *cnt = up ? p1.cnt[1] : p0.cnt[1];
+    int2 *lk = up ? p1.lk : p0.lk;
+    int *cnt = up ? p1.cnt[1] : p0.cnt[1];
     if ((r & 1) == 0) {
-        prv[r] = NIL;
-        nxt[r] = (r + 1 < n) ? (int)(r + 1) : NIL;
+        lk[r] = make_int2(NIL, (r + 1 < n) ? (int)(r + 1) : NIL);
         cnt[r] = 0;
     } else {
-        prv[r] = (int)(r - 1);
-        nxt[r] = NIL;
+        lk[r] = make_int2((int)(r - 1), NIL);
     }
 }
 
@@ -44,8 +43,9 @@ void launch_level1(int64_t n, PassBufs *passes, int npass, int32_t *status, cuda
 // ---------------------------------------------------------------------------
 // One level in global memory, one thread per merge.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_level(Points pts, int64_t n, int level, PassBufs p0, PassBufs p1,
-                                               int32_t *status)
+template <int MINB>
+__global__ void __launch_bounds__(128, MINB) k_level(Points pts, int64_t n, int level, PassBufs p0, PassBufs p1,
+                                                     int32_t *status)
 {
     if (*status) return;
     int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -62,14 +62,15 @@ __global__ void __launch_bounds__(128) k_level(Points pts, int64_t n, int level,
     unsigned *Wdst = upper ? p1.W[dst] : p0.W[dst];
     int *Adst = upper ? p1.A[dst] : p0.A[dst], *Bdst = upper ? p1.B[dst] : p0.B[dst];
     int nl = csrc[lo], nr = csrc[mid];
-    GPts gp{ pts.X, pts.Y, pts.Z, pts.ID };
-    GLinks lk{ upper ? p1.prv : p0.prv, upper ? p1.nxt : p0.nxt };
+    GPts gp{ pts.P };
+    GLinks lk{ upper ? p1.lk : p0.lk };
     GEvIn L{ Wsrc + 2 * lo }, R{ Wsrc + 2 * mid };
     GEvOut out{ Wdst + 2 * lo, Adst + 2 * lo, Bdst + 2 * lo };
     int err = 0;
-    int k = kinetic_merge(gp, lk, (int)mid, L, nl, R, nr, out, (int)(2 * (hi - lo)), upper, &err);
+    int k = kinetic_merge(gp, lk, (int)mid - 1, (int)mid, (int)mid, L, nl, R, nr, out, (int)(2 * (hi - lo)), upper, &err);
     cdst[lo] = k;
     if (err) set_status2(status, HULL3D_ERR_INTERNAL);
+    atomicAdd((upper ? p1.lev_events : p0.lev_events) + level, (unsigned long long)k);
 }
 
 // The last node of a level may have no right child: its movie is the child's.
@@ -92,11 +93,173 @@ __global__ void k_passthrough(int64_t lo, int level, PassBufs p0, PassBufs p1, i
 }
 
 void launch_level(const Points &pts, int64_t n, int level, PassBufs *passes, int npass, int32_t *status,
-                  cudaStream_t st)
+                  cudaStream_t st, int occupancy)
 {
     int64_t nodes = (n + (1ll << level) - 1) >> level;
     dim3 g((unsigned)((nodes + 127) / 128), npass);
-    k_level<<<g, 128, 0, st>>>(pts, n, level, passes[0], passes[npass - 1], status);
+    if (occupancy >= 4) k_level<4><<<g, 128, 0, st>>>(pts, n, level, passes[0], passes[npass - 1], status);
+    else k_level<1><<<g, 128, 0, st>>>(pts, n, level, passes[0], passes[npass - 1], status);
+    int64_t lo = (nodes - 1) << level;
+    if (lo + (1ll << (level - 1)) >= n) {
+        int64_t cap = 2 * (n - lo);
+        unsigned blocks = (unsigned)((cap + 255) / 256);
+        if (blocks > 1024) blocks = 1024;
+        k_passthrough<<<dim3(blocks, npass), 256, 0, st>>>(lo, level, passes[0], passes[npass - 1], status);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Upper levels: one warp per merge on a compacted copy in shared memory.
+// The points a merge can touch are the event points of its two children plus
+// the four x-extremes (lo, mid-1, mid, hi-1): an x-extreme of a child is on
+// the child's hull at every time, every other hull vertex has an event, and
+// the links of these points (t = -inf hull links, or event-time links) only
+// lead to such points.  The warp gathers them -- child movies read
+// coalesced -- into a slot table (a rank -> slot map in global scratch makes
+// each point's slot unique), one lane runs the serial merge at shared-memory
+// latency, and the warp writes the links and the parent movie back.
+// ---------------------------------------------------------------------------
+struct CEvIn {
+    const unsigned *W;
+    __device__ __forceinline__ unsigned w(int i) const { return W[i]; }
+};
+struct CEvOut {  // slots stay in shared memory (backward pass), ranks go to global memory
+    unsigned *S, *W;
+    int *A, *B;
+    const int *RK;
+    __device__ __forceinline__ void put(int k, unsigned w, int a, int b)
+    {
+        S[k] = w;
+        W[k] = (unsigned)RK[w & RANK_MASK] | (w & INS_BIT);
+        A[k] = RK[a];
+        B[k] = RK[b];
+    }
+    __device__ __forceinline__ unsigned w(int k) const { return S[k]; }
+};
+
+constexpr int CMP_THREADS = 32;
+
+__global__ void __launch_bounds__(CMP_THREADS) k_level_cmp(Points pts, int64_t n, int level, PassBufs p0, PassBufs p1,
+                                                           int scap, int32_t *status)
+{
+    extern __shared__ int sm[];
+    __shared__ int s_k, s_bad;
+    if (*status) return;
+    const bool upper = blockIdx.y != 0;
+    const int64_t lo = (int64_t)blockIdx.x << level;
+    if (lo >= n) return;
+    const int64_t half = 1ll << (level - 1);
+    const int64_t mid = lo + half, hi = (lo + 2 * half < n) ? lo + 2 * half : n;
+    if (mid >= hi) return;  // pass-through nodes are copied by k_passthrough
+    const int src = (level - 1) & 1, dst = level & 1;
+    const int *csrc = upper ? p1.cnt[src] : p0.cnt[src];
+    int *cdst = upper ? p1.cnt[dst] : p0.cnt[dst];
+    const unsigned *Wsrc = upper ? p1.W[src] : p0.W[src];
+    unsigned *Wdst = upper ? p1.W[dst] : p0.W[dst];
+    int *Adst = upper ? p1.A[dst] : p0.A[dst], *Bdst = upper ? p1.B[dst] : p0.B[dst];
+    int2 *glk = upper ? p1.lk : p0.lk;
+    int *gmap = upper ? p1.gmap : p0.gmap;
+    const int nl = csrc[lo], nr = csrc[mid];
+    const int ns = nl + nr + 4;
+    const int tid = threadIdx.x;
+    const int cap = (int)(2 * (hi - lo));
+    if (ns > scap) {  // too big for the table: the plain global-memory merge
+        if (tid == 0) {
+            GPts gp{ pts.P };
+            GLinks lk{ glk };
+            GEvIn L{ Wsrc + 2 * lo }, R{ Wsrc + 2 * mid };
+            GEvOut out{ Wdst + 2 * lo, Adst + 2 * lo, Bdst + 2 * lo };
+            int err = 0;
+            int k = kinetic_merge(gp, lk, (int)mid - 1, (int)mid, (int)mid, L, nl, R, nr, out, cap, upper, &err);
+            cdst[lo] = k;
+            if (err) set_status2(status, HULL3D_ERR_INTERNAL);
+            atomicAdd((upper ? p1.lev_events : p0.lev_events) + level, (unsigned long long)k);
+        }
+        return;
+    }
+    int4 *sPt = (int4 *)sm;                   // slot -> (x, y, z, input index)
+    int2 *sLk = (int2 *)(sPt + scap);         // slot -> (prev, next) slots
+    int *sRK = (int *)(sLk + scap);           // slot -> rank
+    unsigned *sIn = (unsigned *)(sRK + scap);  // the two child movies as slots (nl + nr <= scap)
+    unsigned *sOut = sIn + scap;              // the parent movie as slots (<= 2 scap)
+    const unsigned *Lw = Wsrc + 2 * lo, *Rw = Wsrc + 2 * mid;
+    const int e0 = (int)lo, e1 = (int)mid - 1, e2 = (int)mid, e3 = (int)hi - 1;
+    // entry e: 0..3 the x-extremes, then the left movie, then the right movie
+    auto entry = [&](int e) -> unsigned {
+        return e < 4 ? (unsigned)(e == 0 ? e0 : e == 1 ? e1 : e == 2 ? e2 : e3)
+                     : (e < 4 + nl ? Lw[e - 4] : Rw[e - 4 - nl]);
+    };
+    if (tid == 0) s_bad = 0;
+    for (int e = tid; e < ns; e += CMP_THREADS) gmap[entry(e) & RANK_MASK] = 0x7fffffff;
+    __syncthreads();
+    for (int e = tid; e < ns; e += CMP_THREADS) atomicMin(&gmap[entry(e) & RANK_MASK], e);
+    __syncthreads();
+    // slot of a linked rank, checked against the table (never indexes out of it)
+    auto slot_of = [&](int r) -> int {
+        if (r < 0) return NIL;
+        int s = gmap[r];
+        if (s < 0 || s >= ns || (int)(entry(s) & RANK_MASK) != r) { s_bad = 1; return NIL; }
+        return s;
+    };
+    for (int e = tid; e < ns; e += CMP_THREADS) {
+        unsigned raw = entry(e);
+        int r = (int)(raw & RANK_MASK);
+        int s = gmap[r];
+        if (e >= 4) sIn[e - 4] = (unsigned)s | (raw & INS_BIT);
+        if (s == e) {
+            sPt[e] = pts.P[r];
+            sRK[e] = r;
+            int2 l = glk[r];
+            sLk[e] = make_int2(slot_of(l.x), slot_of(l.y));
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int k = 0;
+        if (!s_bad) {
+            CPts cp{ sPt, sRK };
+            CLinks lk{ sLk };
+            CEvIn L{ sIn }, R{ sIn + nl };
+            CEvOut out{ sOut, Wdst + 2 * lo, Adst + 2 * lo, Bdst + 2 * lo, sRK };
+            int err = 0;
+            k = kinetic_merge(cp, lk, gmap[e1], gmap[e2], (int)mid, L, nl, R, nr, out, min(cap, 2 * scap), upper,
+                              &err);
+            if (err) s_bad = 1;
+        }
+        s_k = k;
+    }
+    __syncthreads();
+    if (s_bad) {
+        if (tid == 0) set_status2(status, HULL3D_ERR_INTERNAL);
+        return;
+    }
+    for (int e = tid; e < ns; e += CMP_THREADS) {
+        int r = (int)(entry(e) & RANK_MASK);
+        if (gmap[r] == e) {
+            int2 l = sLk[e];
+            glk[r] = make_int2(l.x < 0 ? NIL : sRK[l.x], l.y < 0 ? NIL : sRK[l.y]);
+        }
+    }
+    if (tid == 0) {
+        cdst[lo] = s_k;
+        atomicAdd((upper ? p1.lev_events : p0.lev_events) + level, (unsigned long long)s_k);
+    }
+}
+
+size_t cmp_smem_bytes(int scap) { return (size_t)scap * (sizeof(int4) + sizeof(int2) + 4 * sizeof(int)); }
+
+void launch_level_cmp(const Points &pts, int64_t n, int level, PassBufs *passes, int npass, int32_t *status,
+                      cudaStream_t st, int scap)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_level_cmp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cmp_smem_bytes(4096));
+        attr_set = true;
+    }
+    int64_t nodes = (n + (1ll << level) - 1) >> level;
+    dim3 g((unsigned)nodes, npass);
+    k_level_cmp<<<g, CMP_THREADS, cmp_smem_bytes(scap), st>>>(pts, n, level, passes[0], passes[npass - 1], scap,
+                                                              status);
     int64_t lo = (nodes - 1) << level;
     if (lo + (1ll << (level - 1)) >= n) {
         int64_t cap = 2 * (n - lo);
@@ -131,24 +294,24 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_fused(Points pts, int64_t n, 
     const int Bcap = 1 << l1;
     const int64_t base = blockIdx.x * (int64_t)Bcap;
     const int B = (int)((base + Bcap <= n) ? Bcap : n - base);
-    int *sX = sm, *sY = sX + Bcap, *sZ = sY + Bcap, *sID = sZ + Bcap;
-    int *sP = sID + Bcap, *sN = sP + Bcap;
-    unsigned *sW0 = (unsigned *)(sN + Bcap), *sW1 = sW0 + 2 * Bcap;
+    int4 *sPt = (int4 *)sm;
+    int2 *sLk = (int2 *)(sPt + Bcap);
+    unsigned *sW0 = (unsigned *)(sLk + Bcap), *sW1 = sW0 + 2 * Bcap;
     int *sC0 = (int *)(sW1 + 2 * Bcap), *sC1 = sC0 + Bcap;
-    for (int i = threadIdx.x; i < B; i += blockDim.x) {
-        sX[i] = pts.X[base + i]; sY[i] = pts.Y[base + i]; sZ[i] = pts.Z[base + i]; sID[i] = pts.ID[base + i];
-    }
-    SPts sp{ sX, sY, sZ, sID, (int)base };
-    SLinks lk{ sP, sN, (int)base };
+    for (int i = threadIdx.x; i < B; i += blockDim.x) sPt[i] = pts.P[base + i];
+    SPts sp{ sPt, (int)base };
+    SLinks lk{ sLk, (int)base };
+    __shared__ unsigned lev_cnt[2][16];
+    if (threadIdx.x < 32) lev_cnt[threadIdx.x >> 4][threadIdx.x & 15] = 0;
     int err = 0;
     for (int pass = 0; pass < npass; pass++) {
         const bool upper = pass != 0;
         unsigned *gW = upper ? p1.W[l1 & 1] : p0.W[l1 & 1];
         int *gA = upper ? p1.A[l1 & 1] : p0.A[l1 & 1], *gB = upper ? p1.B[l1 & 1] : p0.B[l1 & 1];
         int *gcnt = upper ? p1.cnt[l1 & 1] : p0.cnt[l1 & 1];
-        int *gprv = upper ? p1.prv : p0.prv, *gnxt = upper ? p1.nxt : p0.nxt;
+        int2 *glk = upper ? p1.lk : p0.lk;
         __syncthreads();
-        for (int i = threadIdx.x; i < B; i += blockDim.x) { sP[i] = NIL; sN[i] = NIL; sC0[i] = 0; }
+        for (int i = threadIdx.x; i < B; i += blockDim.x) { sLk[i] = make_int2(NIL, NIL); sC0[i] = 0; }
         __syncthreads();
         // a partial last block stops at its own top level; the node above it
         // has no right child, so its movie is the same
@@ -173,26 +336,33 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_fused(Points pts, int64_t n, 
                 int k;
                 if (last) {
                     GEvOut out{ gW + 2 * glo, gA + 2 * glo, gB + 2 * glo };
-                    k = kinetic_merge(sp, lk, (int)(base + lmid), L, Csrc[llo], R, Csrc[lmid], out,
-                                      2 * (lhi - llo), upper, &err);
+                    k = kinetic_merge(sp, lk, (int)(base + lmid) - 1, (int)(base + lmid), (int)(base + lmid), L,
+                                      Csrc[llo], R, Csrc[lmid], out, 2 * (lhi - llo), upper, &err);
                 } else {
                     SEvOut out{ Wdst + 2 * llo };
-                    k = kinetic_merge(sp, lk, (int)(base + lmid), L, Csrc[llo], R, Csrc[lmid], out,
-                                      2 * (lhi - llo), upper, &err);
+                    k = kinetic_merge(sp, lk, (int)(base + lmid) - 1, (int)(base + lmid), (int)(base + lmid), L,
+                                      Csrc[llo], R, Csrc[lmid], out, 2 * (lhi - llo), upper, &err);
                 }
                 Cdst[llo] = k;
+                if (k) atomicAdd(&lev_cnt[pass][level], (unsigned)k);
             }
             __syncthreads();
         }
         // write back links and the level-l1 count of this block's node
         int *Cfin = (top & 1) ? sC1 : sC0;
-        for (int i = threadIdx.x; i < B; i += blockDim.x) { gprv[base + i] = sP[i]; gnxt[base + i] = sN[i]; }
+        for (int i = threadIdx.x; i < B; i += blockDim.x) glk[base + i] = sLk[i];
         if (threadIdx.x == 0) gcnt[base] = Cfin[0];
     }
     if (err) set_status2(status, HULL3D_ERR_INTERNAL);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int ps = threadIdx.x >> 4, lv = threadIdx.x & 15;
+        unsigned c = lev_cnt[ps][lv];
+        if (c && ps < npass) atomicAdd((ps ? p1.lev_events : p0.lev_events) + lv, (unsigned long long)c);
+    }
 }
 
-size_t fused_smem_bytes(int l1) { return (size_t)(1 << l1) * sizeof(int) * 12; }
+size_t fused_smem_bytes(int l1) { return (size_t)(1 << l1) * (sizeof(int4) + sizeof(int2) + 6 * sizeof(int)); }
 
 void launch_fused(const Points &pts, int64_t n, int l0, int l1, PassBufs *passes, int npass, int32_t *status,
                   cudaStream_t st)
@@ -206,7 +376,11 @@ void launch_fused(const Points &pts, int64_t n, int l0, int l1, PassBufs *passes
         cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem_bytes(10));
         attr_set = true;
     }
-    k_fused<<<(unsigned)blocks, FUSED_THREADS, smem, st>>>(pts, n, l1, passes[0], passes[npass - 1], npass, status);
+    // one thread per bottom merge: 2^(l1-1) threads, at least a warp
+    int threads = 1 << (l1 - 1);
+    if (threads < 32) threads = 32;
+    if (threads > FUSED_THREADS) threads = FUSED_THREADS;
+    k_fused<<<(unsigned)blocks, threads, smem, st>>>(pts, n, l1, passes[0], passes[npass - 1], npass, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -230,7 +404,7 @@ __global__ void k_face_keys(Points pts, int64_t n, int level, PassBufs p0, PassB
     const unsigned *W_ = upper ? p1.W[buf] : p0.W[buf];
     const int *A_ = upper ? p1.A[buf] : p0.A[buf], *B_ = upper ? p1.B[buf] : p0.B[buf];
     int w = (int)(W_[e] & RANK_MASK), a = A_[e], b = B_[e];
-    GPts gp{ pts.X, pts.Y, pts.Z, pts.ID };
+    GPts gp{ pts.P };
     P3 A = gp.get(a), W = gp.get(w), Bp = gp.get(b);
     // lower faces are oriented with the normal (w - a) x (b - a) pointing down
     // (Y~ < 0), upper faces with it pointing up

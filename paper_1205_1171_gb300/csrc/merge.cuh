@@ -1,6 +1,7 @@
 // merge.cuh -- one kinetic movie merge (White & Wortman, Sec. 2 "merge step"; the
 // act() and time() figures of Sec. 3), templated over where the points, links
-// and event lists live (global memory or a CTA's shared memory).
+// and event lists live (global memory, a CTA's shared memory, or a compacted
+// slot table).
 //
 // A node covers the ranks [lo, hi) with children [lo, mid) and [mid, hi).  On
 // entry the links hold both children's t = -inf hulls and every child event
@@ -15,6 +16,10 @@
 //      parent's t = -inf hull and the event-time links of its event points.
 // Each output event records the event point (bit 31 set for an insertion) and
 // its left/right neighbours at the event, i.e. one face of the node's hull.
+//
+// The event loop is written for a small instruction footprint: the six
+// candidates live in a short array walked by non-unrolled loops with one call
+// site for the time comparison (unrolling it overflowed the instruction cache).
 #pragma once
 #include "predicates.cuh"
 
@@ -24,28 +29,35 @@ constexpr int NIL = -1;
 constexpr unsigned INS_BIT = 0x80000000u;
 constexpr unsigned RANK_MASK = 0x7fffffffu;
 
-// A candidate event: a triple of ranks with its cached Z, Y and sign(Y~).
+// A candidate event: a triple of point indices with its normal N = (q-p) x (r-p)
+// cached as Z = -N.y, Y = N.z and Nx = N.x, and s = sign(Y~).
 struct Tri {
     int p, q, r;
-    long long Z, Y;
-    int s;
-    bool fin;  // false: a member is NIL (time +inf)
+    int s;  // 0: a member is NIL (time +inf)
+    long long Z, Y, Nx;
 };
 
 template <class PT>
 __device__ __forceinline__ void tri_make(const PT &pt, Tri &t, int p, int q, int r)
 {
     t.p = p; t.q = q; t.r = r;
-    t.fin = (p >= 0) & (q >= 0) & (r >= 0);
-    if (!t.fin) return;
+    if ((p | q | r) < 0) { t.s = 0; return; }
     P3 P = pt.get(p), Q = pt.get(q), R = pt.get(r);
-    zy3(P, Q, R, t.Z, t.Y);
-    t.s = t.Y ? sgn64(t.Y) : turn_slow(P, Q, R);
+    long long ax = Q.x - P.x, ay = Q.y - P.y, az = Q.z - P.z;
+    long long bx = R.x - P.x, by = R.y - P.y, bz = R.z - P.z;
+    t.Z = ax * bz - bx * az;
+    t.Y = ax * by - bx * ay;
+    t.Nx = ay * bz - az * by;
+    // sign(Y~) = first nonzero of (N.z, -N.x, -N.y), else the eta tier
+    if (t.Y) t.s = sgn64(t.Y);
+    else if (t.Nx) t.s = -sgn64(t.Nx);
+    else if (t.Z) t.s = sgn64(t.Z);  // -N.y = Z
+    else t.s = turn_slow(P, Q, R);
 }
 
 // sign(t(a) - t(b)) in the pass's time direction, both finite.
 template <class PT>
-__device__ __forceinline__ int tri_cmp(const PT &pt, const Tri &a, const Tri &b, bool upper)
+__device__ __noinline__ int tri_cmp(const PT &pt, const Tri &a, const Tri &b, bool upper)
 {
     i128 D0 = (i128)a.Z * b.Y - (i128)b.Z * a.Y;
     int s;
@@ -54,9 +66,12 @@ __device__ __forceinline__ int tri_cmp(const PT &pt, const Tri &a, const Tri &b,
     } else if (a.p == b.p && a.q == b.q && a.r == b.r) {
         s = 0;
     } else {
-        P3 A[3] = { pt.get(a.p), pt.get(a.q), pt.get(a.r) };
-        P3 B[3] = { pt.get(b.p), pt.get(b.q), pt.get(b.r) };
-        s = time_cmp_slow(A, B, a.s, b.s);
+        // shear tiers: -c.z then -c.y with c = N1 x N2, N = (Nx, -Z, Y)
+        i128 cz = (i128)a.Z * b.Nx - (i128)a.Nx * b.Z;
+        i128 cy = (i128)a.Y * b.Nx - (i128)a.Nx * b.Y;
+        if (cz != 0) s = -sgn128(cz) * a.s * b.s;
+        else if (cy != 0) s = -sgn128(cy) * a.s * b.s;
+        else s = time_cmp_index(pt, a.p, a.q, a.r, b.p, b.q, b.r, a.s * b.s);
     }
     return upper ? -s : s;
 }
@@ -71,24 +86,27 @@ __device__ __forceinline__ int turn3(const PT &pt, int p, int q, int r)
 template <class LK>
 __device__ __forceinline__ void act(LK &lk, int w)
 {
-    int pw = lk.prv(w), nw = lk.nxt(w);
-    if (lk.nxt(pw) != w) {
-        lk.set_nxt(pw, w);
-        lk.set_prv(nw, w);
+    int2 lw = lk.get(w);
+    if (lk.nxt(lw.x) != w) {
+        lk.set_nxt(lw.x, w);
+        lk.set_prv(lw.y, w);
     } else {
-        lk.set_nxt(pw, nw);
-        lk.set_prv(nw, pw);
+        lk.set_nxt(lw.x, lw.y);
+        lk.set_prv(lw.y, lw.x);
     }
 }
 
-// Returns the number of parent events written to `out` (at most cap); on an
-// overflow (impossible for valid input) sets *err and returns cap.
+// Points are addressed by an index that is either the rank itself or a slot
+// of a compacted table; pt.rk(i) gives the rank (the perturbed x-order).
+// u0 and v0 address the ranks mid - 1 and mid.  Returns the number of parent
+// events written to `out` (at most cap); on an overflow (impossible for valid
+// input) sets *err and returns cap.
 template <class PT, class LK, class EIN, class EOUT>
-__device__ int kinetic_merge(const PT &pt, LK &lk, int mid, const EIN &L, int nl, const EIN &R, int nr, EOUT &out,
-                             int cap, bool upper, int *err)
+__device__ int kinetic_merge(const PT &pt, LK &lk, int u0, int v0, int mid, const EIN &L, int nl, const EIN &R,
+                             int nr, EOUT &out, int cap, bool upper, int *err)
 {
     // 1. bridge at t = -inf; u only moves left and v only right, so this ends
-    int u = mid - 1, v = mid;
+    int u = u0, v = v0;
     for (;;) {
         int vn = lk.nxt(v);
         if (vn != NIL && turn3(pt, u, v, vn) < 0) { v = vn; continue; }
@@ -99,64 +117,65 @@ __device__ int kinetic_merge(const PT &pt, LK &lk, int mid, const EIN &L, int nl
 
     // 2. forward pass
     Tri c[6];
-    bool valid[6];
+    unsigned valid = 0;  // bit l: candidate l is finite and later than the last event
 #pragma unroll
-    for (int l = 0; l < 6; l++) { c[l].p = c[l].q = c[l].r = -2; c[l].fin = false; valid[l] = false; }
+    for (int l = 0; l < 6; l++) { c[l].p = c[l].q = c[l].r = -2; c[l].s = 0; }
     Tri old;
     bool have_old = false;
     int i = 0, j = 0, k = 0;
     for (;;) {
-        int tp[6], tq[6], tr[6];
-        if (i < nl) { int e = (int)(L.w(i) & RANK_MASK); tp[0] = lk.prv(e); tq[0] = e; tr[0] = lk.nxt(e); }
-        else { tp[0] = tq[0] = tr[0] = NIL; }
-        if (j < nr) { int e = (int)(R.w(j) & RANK_MASK); tp[1] = lk.prv(e); tq[1] = e; tr[1] = lk.nxt(e); }
-        else { tp[1] = tq[1] = tr[1] = NIL; }
-        int un = lk.nxt(u), upv = lk.prv(u), vp = lk.prv(v), vn = lk.nxt(v);
-        tp[2] = u;   tq[2] = un; tr[2] = v;
-        tp[3] = upv; tq[3] = u;  tr[3] = v;
-        tp[4] = u;   tq[4] = vp; tr[4] = v;
-        tp[5] = u;   tq[5] = v;  tr[5] = vn;
+        const int e0 = i < nl ? (int)(L.w(i) & RANK_MASK) : NIL;
+        const int e1 = j < nr ? (int)(R.w(j) & RANK_MASK) : NIL;
+        const int2 l0 = e0 >= 0 ? lk.get(e0) : make_int2(NIL, NIL);
+        const int2 l1 = e1 >= 0 ? lk.get(e1) : make_int2(NIL, NIL);
+        const int2 lu = lk.get(u), lv = lk.get(v);
         // refresh the candidates whose triple changed; an unchanged candidate
         // keeps its validity (it was later than the previous event, hence
         // later than the one just taken, which had a different triple)
-#pragma unroll
+#pragma unroll 1
         for (int l = 0; l < 6; l++) {
-            if (tp[l] != c[l].p || tq[l] != c[l].q || tr[l] != c[l].r) {
-                tri_make(pt, c[l], tp[l], tq[l], tr[l]);
-                valid[l] = c[l].fin && (!have_old || tri_cmp(pt, c[l], old, upper) > 0);
+            int tp, tq, tr;
+            switch (l) {
+            case 0: tp = l0.x; tq = e0; tr = l0.y; break;  // next event of the left child
+            case 1: tp = l1.x; tq = e1; tr = l1.y; break;  // next event of the right child
+            case 2: tp = u; tq = lu.y; tr = v; break;      // u advances to u.next
+            case 3: tp = lu.x; tq = u; tr = v; break;      // u retreats to u.prev
+            case 4: tp = u; tq = lv.x; tr = v; break;      // v retreats to v.prev
+            default: tp = u; tq = v; tr = lv.y; break;     // v advances to v.next
+            }
+            if (tp != c[l].p || tq != c[l].q || tr != c[l].r) {
+                tri_make(pt, c[l], tp, tq, tr);
+                bool ok = c[l].s != 0 && (!have_old || tri_cmp(pt, c[l], old, upper) > 0);
+                valid = ok ? (valid | (1u << l)) : (valid & ~(1u << l));
             }
         }
         int best = -1;
-        Tri bt;
-#pragma unroll
+#pragma unroll 1
         for (int l = 0; l < 6; l++)
-            if (valid[l] && (best < 0 || tri_cmp(pt, c[l], bt, upper) < 0)) { best = l; bt = c[l]; }
+            if (((valid >> l) & 1u) && (best < 0 || tri_cmp(pt, c[l], c[best], upper) < 0)) best = l;
         if (best < 0) break;
         if (k >= cap) { *err = 1; return cap; }
-        switch (best) {
-        case 0: {
-            int e = tq[0];
-            i++;
-            if (e < u) out.put(k++, (unsigned)e | (lk.nxt(tp[0]) != e ? INS_BIT : 0u), tp[0], tr[0]);
+        const Tri t = c[best];
+        // apply the event (its triple t is: left neighbour, point, right neighbour)
+        if (best <= 1) {
+            const int e = t.q;
+            bool vis;
+            if (best == 0) { i++; vis = pt.rk(e) < pt.rk(u); }
+            else { j++; vis = pt.rk(e) > pt.rk(v); }
+            if (vis) out.put(k++, (unsigned)e | (lk.nxt(t.p) != e ? INS_BIT : 0u), t.p, t.r);
             act(lk, e);
-            break;
+        } else {
+            // bridge events: c2 and c4 insert the new bridge end, c3 and c5 delete the old one
+            const bool ins = (best == 2) | (best == 4);
+            out.put(k++, (unsigned)t.q | (ins ? INS_BIT : 0u), t.p, t.r);
+            if (best == 2) u = t.q;
+            else if (best == 3) u = t.p;
+            else if (best == 4) v = t.q;
+            else v = t.r;
         }
-        case 1: {
-            int e = tq[1];
-            j++;
-            if (e > v) out.put(k++, (unsigned)e | (lk.nxt(tp[1]) != e ? INS_BIT : 0u), tp[1], tr[1]);
-            act(lk, e);
-            break;
-        }
-        case 2: out.put(k++, (unsigned)un | INS_BIT, u, v); u = un; break;
-        case 3: out.put(k++, (unsigned)u, upv, v); u = upv; break;
-        case 4: out.put(k++, (unsigned)vp | INS_BIT, u, v); v = vp; break;
-        default: out.put(k++, (unsigned)v, u, vn); v = vn; break;
-        }
-        old = bt;
+        old = t;
         have_old = true;
-#pragma unroll
-        for (int l = 0; l < 6; l++) valid[l] = valid[l] && (l != best);  // static indices keep c[] in registers
+        valid &= ~(1u << best);
     }
 
     // 3. backward pass from the t = +inf bridge
@@ -164,32 +183,42 @@ __device__ int kinetic_merge(const PT &pt, LK &lk, int mid, const EIN &L, int nl
     lk.set_prv(v, u);
     for (int kk = k - 1; kk >= 0; kk--) {
         int w = (int)(out.w(kk) & RANK_MASK);
-        if (w <= u || w >= v) {
+        const int rw = pt.rk(w);
+        if (rw <= pt.rk(u) || rw >= pt.rk(v)) {
             act(lk, w);
             if (w == u) u = lk.prv(u);
             else if (w == v) v = lk.nxt(v);
         } else {
-            lk.set_nxt(u, w); lk.set_prv(w, u);
-            lk.set_prv(v, w); lk.set_nxt(w, v);
-            if (w < mid) u = w; else v = w;
+            lk.set_nxt(u, w);
+            lk.set(w, make_int2(u, v));
+            lk.set_prv(v, w);
+            if (rw < mid) u = w; else v = w;
         }
     }
     return k;
 }
 
 // ---- storage adapters -------------------------------------------------------
+// Points are packed as int4 (x, y, z, input index); links as int2 (prev, next).
 
-struct GPts {  // sorted SoA in global memory, indexed by rank
-    const int *X, *Y, *Z, *ID;
-    __device__ __forceinline__ P3 get(int r) const { return P3{ X[r], Y[r], Z[r], ID[r], r }; }
+struct GPts {  // rank-ordered points in global memory
+    const int4 *P;
+    __device__ __forceinline__ P3 get(int r) const
+    {
+        int4 p = P[r];
+        return P3{ p.x, p.y, p.z, p.w, r };
+    }
+    __device__ __forceinline__ int rk(int r) const { return r; }
 };
 
 struct GLinks {
-    int *P, *N;
-    __device__ __forceinline__ int prv(int r) const { return P[r]; }
-    __device__ __forceinline__ int nxt(int r) const { return N[r]; }
-    __device__ __forceinline__ void set_prv(int r, int v) { P[r] = v; }
-    __device__ __forceinline__ void set_nxt(int r, int v) { N[r] = v; }
+    int2 *L;
+    __device__ __forceinline__ int2 get(int r) const { return L[r]; }
+    __device__ __forceinline__ int prv(int r) const { return L[r].x; }
+    __device__ __forceinline__ int nxt(int r) const { return L[r].y; }
+    __device__ __forceinline__ void set(int r, int2 v) { L[r] = v; }
+    __device__ __forceinline__ void set_prv(int r, int v) { L[r].x = v; }
+    __device__ __forceinline__ void set_nxt(int r, int v) { L[r].y = v; }
 };
 
 struct GEvIn {  // a movie in global memory
@@ -206,22 +235,47 @@ struct GEvOut {
 
 // Shared-memory variants: arrays hold one block of ranks starting at `base`.
 struct SPts {
-    const int *X, *Y, *Z, *ID;
+    const int4 *P;
     int base;
     __device__ __forceinline__ P3 get(int r) const
     {
-        int i = r - base;
-        return P3{ X[i], Y[i], Z[i], ID[i], r };
+        int4 p = P[r - base];
+        return P3{ p.x, p.y, p.z, p.w, r };
     }
+    __device__ __forceinline__ int rk(int r) const { return r; }
 };
 
 struct SLinks {
-    int *P, *N;
+    int2 *L;
     int base;
-    __device__ __forceinline__ int prv(int r) const { return P[r - base]; }
-    __device__ __forceinline__ int nxt(int r) const { return N[r - base]; }
-    __device__ __forceinline__ void set_prv(int r, int v) { P[r - base] = v; }
-    __device__ __forceinline__ void set_nxt(int r, int v) { N[r - base] = v; }
+    __device__ __forceinline__ int2 get(int r) const { return L[r - base]; }
+    __device__ __forceinline__ int prv(int r) const { return L[r - base].x; }
+    __device__ __forceinline__ int nxt(int r) const { return L[r - base].y; }
+    __device__ __forceinline__ void set(int r, int2 v) { L[r - base] = v; }
+    __device__ __forceinline__ void set_prv(int r, int v) { L[r - base].x = v; }
+    __device__ __forceinline__ void set_nxt(int r, int v) { L[r - base].y = v; }
+};
+
+// Compacted table in shared memory: slot -> point, with its rank.
+struct CPts {
+    const int4 *P;
+    const int *RK;
+    __device__ __forceinline__ P3 get(int s) const
+    {
+        int4 p = P[s];
+        return P3{ p.x, p.y, p.z, p.w, RK[s] };
+    }
+    __device__ __forceinline__ int rk(int s) const { return RK[s]; }
+};
+
+struct CLinks {  // links between slots
+    int2 *L;
+    __device__ __forceinline__ int2 get(int s) const { return L[s]; }
+    __device__ __forceinline__ int prv(int s) const { return L[s].x; }
+    __device__ __forceinline__ int nxt(int s) const { return L[s].y; }
+    __device__ __forceinline__ void set(int s, int2 v) { L[s] = v; }
+    __device__ __forceinline__ void set_prv(int s, int v) { L[s].x = v; }
+    __device__ __forceinline__ void set_nxt(int s, int v) { L[s].y = v; }
 };
 
 }  // namespace hull3d

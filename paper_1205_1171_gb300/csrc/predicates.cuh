@@ -122,11 +122,15 @@ __device__ __forceinline__ long long ww_coef(const long long u[3], const long lo
     }
 }
 
-// sign(t~(A) - t~(B)) for two triples whose unperturbed D vanished; s1, s2 are
-// the signs of Y~(A), Y~(B).  Returns 0 only for equal point sets.
-__device__ __noinline__ int time_cmp_slow(const P3 *A, const P3 *B, int s1, int s2)
+// The index tiers of sign(t~(A) - t~(B)) for two triples whose constant, a and
+// a^2 coefficients of D vanished (their normals are parallel or zero): the
+// gam_i then gam_i eta_j coefficients, indices ascending.  ss = sign(Y~A) sign(Y~B).
+// Returns 0 only for equal point sets.
+template <class PT>
+__device__ __noinline__ int time_cmp_index(const PT &pt, int a0, int a1, int a2, int b0, int b1, int b2, int ss)
 {
-    // equal sets tie
+    const P3 A[3] = { pt.get(a0), pt.get(a1), pt.get(a2) };
+    const P3 B[3] = { pt.get(b0), pt.get(b1), pt.get(b2) };
     {
         int m = 0;
         for (int i = 0; i < 3; i++)
@@ -136,43 +140,49 @@ __device__ __noinline__ int time_cmp_slow(const P3 *A, const P3 *B, int s1, int 
     long long n1x, n1y, n1z, n2x, n2y, n2z;
     normal3(A[0], A[1], A[2], n1x, n1y, n1z);
     normal3(B[0], B[1], B[2], n2x, n2y, n2z);
-    const int ss = s1 * s2;
-    // a, a^2 tiers: -c.z, -c.y with c = N1 x N2 (the constant tier -c.x already vanished)
-    i128 cz = (i128)n1x * n2y - (i128)n1y * n2x;
-    if (cz) return -sgn128(cz) * ss;
-    i128 cy = (i128)n1z * n2x - (i128)n1x * n2z;
-    if (cy) return -sgn128(cy) * ss;
-    // the input indices involved, ascending, without repeats
-    int ids[6], k = 0;
-    for (int i = 0; i < 3; i++) ids[k++] = A[i].id;
-    for (int i = 0; i < 3; i++) {
-        bool dup = false;
-        for (int j = 0; j < 3; j++) dup |= (B[i].id == A[j].id);
-        if (!dup) ids[k++] = B[i].id;
-    }
-    for (int i = 1; i < k; i++)
-        for (int j = i; j > 0 && ids[j - 1] > ids[j]; j--) {
-            int t = ids[j]; ids[j] = ids[j - 1]; ids[j - 1] = t;
+    // the input indices involved, ascending, visited by repeated minimum search
+    int prev = -1;
+    for (int t = 0; t < 6; t++) {
+        int id = 0x7fffffff;
+        for (int i = 0; i < 3; i++) {
+            if (A[i].id > prev && A[i].id < id) id = A[i].id;
+            if (B[i].id > prev && B[i].id < id) id = B[i].id;
         }
-    // gam_i tiers (eta-free part)
-    for (int t = 0; t < k; t++) {
+        if (id == 0x7fffffff) break;
+        prev = id;
         long long w1[3], w2[3];
-        wcoef(A, ids[t], w1);
-        wcoef(B, ids[t], w2);
+        wcoef(A, id, w1);
+        wcoef(B, id, w2);
         for (int m = 0; m < 10; m++) {
             i128 c = wy_coef(w1, n2x, n2y, n2z, m) - wy_coef(w2, n1x, n1y, n1z, m);
             if (c) return sgn128(c) * ss;
         }
     }
-    // gam_i eta_j tiers: both triples are collinear in 3D
-    for (int tj = 0; tj < k; tj++) {
+    // gam_i eta_j: both triples collinear in 3D; j ascending, then i ascending
+    int pj = -1;
+    for (int tj = 0; tj < 6; tj++) {
+        int jd = 0x7fffffff;
+        for (int i = 0; i < 3; i++) {
+            if (A[i].id > pj && A[i].id < jd) jd = A[i].id;
+            if (B[i].id > pj && B[i].id < jd) jd = B[i].id;
+        }
+        if (jd == 0x7fffffff) break;
+        pj = jd;
         long long u1[3], u2[3];
-        wcoef(A, ids[tj], u1);
-        wcoef(B, ids[tj], u2);
-        for (int ti = 0; ti < k; ti++) {
+        wcoef(A, jd, u1);
+        wcoef(B, jd, u2);
+        int pi = -1;
+        for (int ti = 0; ti < 6; ti++) {
+            int id = 0x7fffffff;
+            for (int i = 0; i < 3; i++) {
+                if (A[i].id > pi && A[i].id < id) id = A[i].id;
+                if (B[i].id > pi && B[i].id < id) id = B[i].id;
+            }
+            if (id == 0x7fffffff) break;
+            pi = id;
             long long w1[3], w2[3];
-            wcoef(A, ids[ti], w1);
-            wcoef(B, ids[ti], w2);
+            wcoef(A, id, w1);
+            wcoef(B, id, w2);
             for (int m = 0; m < 5; m++) {
                 long long c = ww_coef(w1, u2, m) - ww_coef(w2, u1, m);
                 if (c) return sgn64(c) * ss;

@@ -35,25 +35,21 @@ void launch_keys(const int32_t *xyz, int64_t n, uint64_t *keys, uint32_t *vals, 
 }
 
 __global__ void k_decode(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t n,
-                         int32_t *__restrict__ X, int32_t *__restrict__ Y, int32_t *__restrict__ Z,
-                         int32_t *__restrict__ ID, int32_t *status)
+                         int4 *__restrict__ P, int32_t *status)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint64_t k = keys[i];
     const int lo = -(1 << 20);
-    X[i] = (int)((k >> 42) & 0x1fffff) + lo;
-    Z[i] = (int)((k >> 21) & 0x1fffff) + lo;
-    Y[i] = (int)(k & 0x1fffff) + lo;
-    ID[i] = (int32_t)vals[i];
+    P[i] = make_int4((int)((k >> 42) & 0x1fffff) + lo, (int)(k & 0x1fffff) + lo, (int)((k >> 21) & 0x1fffff) + lo,
+                     (int32_t)vals[i]);
     if (i > 0 && keys[i - 1] == k) set_status(status, HULL3D_ERR_DUPLICATE);
 }
 
-void launch_decode(const uint64_t *keys, const uint32_t *vals, int64_t n, int32_t *X, int32_t *Y, int32_t *Z,
-                   int32_t *ID, int32_t *status, cudaStream_t st)
+void launch_decode(const uint64_t *keys, const uint32_t *vals, int64_t n, int4 *P, int32_t *status, cudaStream_t st)
 {
     if (n <= 0) return;
-    k_decode<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(keys, vals, n, X, Y, Z, ID, status);
+    k_decode<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(keys, vals, n, P, status);
 }
 
 // ---------------------------------------------------------------------------

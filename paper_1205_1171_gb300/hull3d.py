@@ -30,10 +30,11 @@ ERR_INTERNAL = 9
 
 # every symbol include/hull3d.h declares
 EXPORTS = (
-    "hull3d_plan", "hull3d_destroy", "hull3d_plan_bytes", "hull3d_compute_async", "hull3d_compute",
+    "hull3d_plan", "hull3d_plan_opts", "hull3d_destroy", "hull3d_plan_bytes", "hull3d_compute_async", "hull3d_compute",
     "hull3d_compute_host", "hull3d_batch_async", "hull3d_strerror", "hull3d_last_cuda_error",
-    "hull3d_last_launch_count",
+    "hull3d_last_launch_count", "hull3d_profile", "hull3d_profile_read", "hull3d_profile_levels", "hull3d_level_events",
 )
+PHASES = ("sort", "fused", "levels", "seg", "faces")
 
 
 class Hull3DError(RuntimeError):
@@ -48,7 +49,8 @@ class Hull3DError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("fused_levels", ctypes.c_int32), ("seg_level", ctypes.c_int32), ("seg_events", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("use_graph", ctypes.c_int32), ("level_occupancy", ctypes.c_int32), ("cmp_level", ctypes.c_int32),
+                ("cmp_slots", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 def load():
@@ -62,6 +64,8 @@ def load():
             P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
             lib.hull3d_plan.argtypes = [ctypes.POINTER(P), i64, i64, ctypes.POINTER(Opts)]
             lib.hull3d_plan.restype = ctypes.c_int
+            lib.hull3d_plan_opts.argtypes = [P, ctypes.POINTER(Opts)]
+            lib.hull3d_plan_opts.restype = ctypes.c_int
             lib.hull3d_destroy.argtypes = [P]
             lib.hull3d_destroy.restype = None
             lib.hull3d_plan_bytes.argtypes = [P]
@@ -80,6 +84,14 @@ def load():
             lib.hull3d_last_cuda_error.restype = ctypes.c_int
             lib.hull3d_last_launch_count.argtypes = [P]
             lib.hull3d_last_launch_count.restype = i64
+            lib.hull3d_profile.argtypes = [P, ctypes.c_int]
+            lib.hull3d_profile.restype = ctypes.c_int
+            lib.hull3d_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
+            lib.hull3d_profile_read.restype = ctypes.c_int
+            lib.hull3d_profile_levels.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+            lib.hull3d_profile_levels.restype = ctypes.c_int
+            lib.hull3d_level_events.argtypes = [P, ctypes.POINTER(i64)]
+            lib.hull3d_level_events.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -112,9 +124,10 @@ class Hull3D:
     """A plan: scratch for hulls of up to max_n points (and batches totalling max_n)."""
 
     def __init__(self, max_n: int, max_clouds: int = 0, fused_levels: int = 0, seg_level: int = 0,
-                 seg_events: int = 0, use_graph: int = 0):
+                 seg_events: int = 0, use_graph: int = 0, level_occupancy: int = 0, cmp_level: int = 0,
+                 cmp_slots: int = 0):
         self._lib = load()
-        opts = Opts(fused_levels, seg_level, seg_events, use_graph)
+        opts = Opts(fused_levels, seg_level, seg_events, use_graph, level_occupancy, cmp_level, cmp_slots)
         plan = ctypes.c_void_p()
         rc = self._lib.hull3d_plan(ctypes.byref(plan), int(max_n), int(max_clouds), ctypes.byref(opts))
         if rc:
@@ -134,12 +147,54 @@ class Hull3D:
             pass
 
     @property
+    def opts(self) -> dict:
+        o = Opts()
+        rc = self._lib.hull3d_plan_opts(self._plan, ctypes.byref(o))
+        if rc:
+            raise Hull3DError(rc, "plan_opts")
+        return {k: getattr(o, k) for k, _ in Opts._fields_ if k != "reserved"}
+
+    @property
+    def fused_levels_used(self) -> int:
+        return int(self.opts["fused_levels"])
+
+    @property
     def scratch_bytes(self) -> int:
         return int(self._lib.hull3d_plan_bytes(self._plan))
 
     @property
     def last_launches(self) -> int:
         return int(self._lib.hull3d_last_launch_count(self._plan))
+
+    def profile(self, enable: bool = True) -> None:
+        rc = self._lib.hull3d_profile(self._plan, int(enable))
+        if rc:
+            raise Hull3DError(rc, "profile")
+
+    def profile_read(self):
+        """({phase: ms summed over recorded calls}, calls)."""
+        ms = (ctypes.c_double * len(PHASES))()
+        calls = ctypes.c_int64(0)
+        rc = self._lib.hull3d_profile_read(self._plan, ms, ctypes.byref(calls))
+        if rc:
+            raise Hull3DError(rc, "profile_read")
+        return {k: ms[i] for i, k in enumerate(PHASES)}, calls.value
+
+    def profile_levels(self) -> np.ndarray:
+        """ms per global merge level over the recorded calls (read before profile_read)."""
+        ms = (ctypes.c_double * 64)()
+        rc = self._lib.hull3d_profile_levels(self._plan, ms)
+        if rc:
+            raise Hull3DError(rc, "profile_levels")
+        return np.array(ms[:])
+
+    def level_events(self) -> np.ndarray:
+        """(2, 64) events written per merge level by the last single-hull call."""
+        out = (ctypes.c_int64 * 128)()
+        rc = self._lib.hull3d_level_events(self._plan, out)
+        if rc:
+            raise Hull3DError(rc, "level_events")
+        return np.array(out[:], dtype=np.int64).reshape(2, 64)
 
     def compute(self, xyz, stream=None):
         """Canonical faces (F, 3) int32 on the device of xyz (synchronous)."""

@@ -62,6 +62,22 @@ def test_fused_depths_agree(H, fused):
         p.close()
 
 
+@pytest.mark.parametrize("cmp_level,cmp_slots", [(2, 1024), (2, 48), (5, 128), (3, 4096), (99, 0)])
+def test_upper_level_kernels_agree(H, cmp_level, cmp_slots):
+    """The compacted warp-per-merge kernel (with its too-big fallback) and the
+    thread-per-merge kernel give the oracle's faces."""
+    p = H.Hull3D(1 << 15, fused_levels=1, cmp_level=cmp_level, cmp_slots=cmp_slots)
+    try:
+        for dist in inputs.DISTS:
+            for n in (5, 77, 1000, 1 << 15):
+                pts = inputs.cloud_seeded(dist, n, 4200 + n + cmp_level)
+                assert np.array_equal(run(p, pts), oracle.hull(pts)), (dist, n)
+        for pts in _tiny_sets(100, 17):
+            assert np.array_equal(run(p, pts), oracle.hull(pts)), pts.tolist()
+    finally:
+        p.close()
+
+
 def test_config_small_cube_4096(plan):
     pts = inputs.cloud_seeded("cube", 4096, inputs.seed_for(1))
     got = run(plan, pts)
