@@ -54,16 +54,18 @@ extern "C" {
 
 typedef struct hull3d_plan_s *hull3d_plan_t;
 
-/* Tuning knobs; zero fields mean "automatic". */
+/* Tuning knobs; zero fields mean "automatic" (hull3d_plan_opts reports the
+ * resolved values).  None of them changes the result, only its speed. */
 typedef struct {
-    int32_t fused_levels;   /* levels merged in shared memory by the fused bottom kernel (1..10) */
-    int32_t seg_level;      /* first level merged time-segment-parallel; < 0 disables */
-    int32_t seg_events;     /* target child events per time segment */
-    int32_t use_graph;      /* 1: replay the level sequence as a CUDA graph (default), -1: plain launches */
-    int32_t level_occupancy; /* global merge kernel: 1 = no register cap, 4 = at most 128 registers (4 CTAs/SM) */
-    int32_t cmp_level;      /* first level merged by the compacted warp-per-merge kernel */
-    int32_t cmp_slots;      /* its shared-memory table size in points (<= 4096) */
-    int32_t reserved[1];
+    int32_t fused_levels;    /* bottom levels merged in one shared-memory kernel (1 = none, up to 10) */
+    int32_t seg_level;       /* first level merged time-segment-parallel (> log2 n: never) */
+    int32_t seg_events;      /* target child events per time window of a segment-parallel merge */
+    int32_t use_graph;       /* 1: replay the level sequence as a CUDA graph, -1: plain launches */
+    int32_t level_occupancy; /* thread-per-merge kernel: 1 = no register cap, 4 = at most 128 registers */
+    int32_t cmp_level;       /* first level merged by the compacted warp-per-merge kernel */
+    int32_t cmp_slots;       /* its shared-memory table size in points (<= 4096) */
+    int32_t seg_slots;       /* shared-memory table size of one time window in points (<= 6144) */
+    int32_t reserved[8];
 } hull3d_opts;
 
 /* Creates a plan for hulls of up to max_n points (hull3d_compute*) and for

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "segmerge.cuh"
 
 using namespace hull3d;
 
@@ -88,6 +89,13 @@ struct hull3d_plan_s {
     int32_t *h_status = nullptr;
     int64_t last_launches = 0;
     unsigned long long *lev_stats = nullptr;  // [2][64]
+    // time-segment-parallel levels
+    SegBufs seg[2]{};
+    uint64_t *pk0 = nullptr, *pk1 = nullptr;
+    uint32_t *pv0 = nullptr, *pv1 = nullptr;
+    unsigned long long *npairs = nullptr;
+    int *overflow = nullptr;
+    int64_t pair_cap = 0, S_cap = 0, M_cap = 0;
     // phase profiling
     bool profile = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -110,6 +118,10 @@ struct Bump {
         return p;
     }
 };
+
+int default_seg_level(const hull3d_plan_s *p);
+int default_seg_events(const hull3d_plan_s *p);
+int default_seg_slots(const hull3d_plan_s *p);
 
 // Lays out every buffer of the plan; with base == nullptr it only measures.
 size_t layout(hull3d_plan_s *p, char *base)
@@ -135,6 +147,49 @@ size_t layout(hull3d_plan_s *p, char *base)
         pb.lk = b.take<int2>(N);
         pb.gmap = b.take<int32_t>(N);
     }
+    // time-segment-parallel levels: window scratch sized for the largest level
+    {
+        int Lmax = 0;
+        while ((1ll << Lmax) < N) Lmax++;
+        const int sl = default_seg_level(p), K = default_seg_events(p);
+        p->S_cap = p->M_cap = 0;
+        for (int lv = sl > 2 ? sl : 2; lv <= Lmax; lv++) {
+            const int64_t M = (N + (1ll << lv) - 1) >> lv;
+            const int64_t smax = ((1ll << (lv + 1)) + K - 1) / K;
+            if (M * smax > p->S_cap) p->S_cap = M * smax;
+            if (M > p->M_cap) p->M_cap = M;
+        }
+        const int64_t ocap = 2 * K + 256;
+        p->pair_cap = p->S_cap ? 4 * N + 8 * p->S_cap : 0;
+        for (int s = 0; s < 2 && p->S_cap; s++) {
+            SegBufs &sb = p->seg[s];
+            sb.bound = b.take<int2>(p->S_cap);
+            sb.nseg = b.take<int>(p->M_cap);
+            sb.ins_idx = b.take<int>(N);
+            sb.del_idx = b.take<int>(N);
+            sb.smap = b.take<int>(N);
+            sb.oW = b.take<unsigned>(p->S_cap * ocap);
+            sb.oA = b.take<int>(p->S_cap * ocap);
+            sb.oB = b.take<int>(p->S_cap * ocap);
+            sb.ocnt = b.take<int>(p->S_cap);
+            sb.bridge0 = b.take<int2>(p->M_cap);
+            sb.nofit = b.take<int>(p->M_cap);
+        }
+        if (p->S_cap) {
+            p->pk0 = b.take<uint64_t>(p->pair_cap);
+            p->pk1 = b.take<uint64_t>(p->pair_cap);
+            p->pv0 = b.take<uint32_t>(p->pair_cap);
+            p->pv1 = b.take<uint32_t>(p->pair_cap);
+            p->npairs = b.take<unsigned long long>(1);
+            p->overflow = b.take<int>(1);
+            // the pair sort needs histogram space for pair_cap items
+            int64_t tiles = (p->pair_cap + SORT_TILE - 1) / SORT_TILE;
+            if (tiles > p->ss.max_tiles) {
+                p->ss.max_tiles = tiles;
+                p->ss.hist = b.take<uint32_t>(256 * tiles);
+            }
+        }
+    }
     p->lev_stats = b.take<unsigned long long>(128);
     p->pass[0].lev_events = p->lev_stats;
     p->pass[1].lev_events = p->lev_stats + 64;
@@ -156,6 +211,9 @@ int default_occupancy(const hull3d_plan_s *p, int level)
 }
 int default_cmp_level(const hull3d_plan_s *p) { return p->opts.cmp_level > 0 ? p->opts.cmp_level : 13; }
 int default_cmp_slots(const hull3d_plan_s *p) { return p->opts.cmp_slots > 0 ? p->opts.cmp_slots : 1024; }
+int default_seg_level(const hull3d_plan_s *p) { return p->opts.seg_level > 0 ? p->opts.seg_level : 14; }
+int default_seg_events(const hull3d_plan_s *p) { return p->opts.seg_events > 0 ? p->opts.seg_events : 512; }
+int default_seg_slots(const hull3d_plan_s *p) { return p->opts.seg_slots > 0 ? p->opts.seg_slots : 2048; }
 
 // Records a phase-boundary event when profiling (one per boundary per call).
 int mark(hull3d_plan_s *p, cudaStream_t st, int *slot)
@@ -214,23 +272,32 @@ int enqueue_hull(hull3d_plan_s *p, const int32_t *d_xyz, int64_t n, int32_t *d_f
     launches++;
     STEP("fused levels");
     MARK(2);
+    bool seg_marked = false;
     for (int level = l1 + 1; level <= L; level++) {
+        const bool seg = level >= default_seg_level(p) && p->S_cap;
+        if (seg && !seg_marked) { MARK(3); seg_marked = true; }
         int lv0 = -1, lv1 = -1;
         if (p->profile) { int r_ = mark(p, st, &lv0); if (r_) return r_; }
-        if (level >= default_cmp_level(p))
-            launch_level_cmp(pts, n, level, p->pass, 2, status, st, default_cmp_slots(p));
-        else
-            launch_level(pts, n, level, p->pass, 2, status, st, default_occupancy(p, level));
+        if (seg) {
+            launch_seg_level(pts, n, level, p->pass, p->seg, p->pk0, p->pv0, p->pk1, p->pv1, p->npairs, p->overflow,
+                             p->pair_cap, p->S_cap, p->M_cap, default_seg_events(p), default_seg_slots(p), p->ss, status,
+                             st, &launches);
+        } else {
+            if (level >= default_cmp_level(p))
+                launch_level_cmp(pts, n, level, p->pass, 2, status, st, default_cmp_slots(p));
+            else
+                launch_level(pts, n, level, p->pass, 2, status, st, default_occupancy(p, level));
+            int64_t last_lo = (((n + (1ll << level) - 1) >> level) - 1) << level;
+            launches += (last_lo + (1ll << (level - 1)) >= n) ? 2 : 1;  // level + pass-through copy
+        }
         if (p->profile) {
             int r_ = mark(p, st, &lv1);
             if (r_) return r_;
             p->level_marks.insert(p->level_marks.end(), { level, lv0, lv1 });
         }
-        int64_t last_lo = (((n + (1ll << level) - 1) >> level) - 1) << level;
-        launches += (last_lo + (1ll << (level - 1)) >= n) ? 2 : 1;  // level + pass-through copy
         STEP("merge level");
     }
-    MARK(3);
+    if (!seg_marked) MARK(3);
     MARK(4);
     int fbits = ceil_log2(n);
     if (fbits < 1) fbits = 1;
@@ -274,7 +341,8 @@ int hull3d_plan(hull3d_plan_t *out, int64_t max_n, int64_t max_clouds, const hul
     p->max_n = max_n < 4 ? 4 : max_n;
     p->max_clouds = max_clouds;
     if (opts) p->opts = *opts;
-    if (p->opts.fused_levels < 0 || p->opts.fused_levels > 10 || p->opts.cmp_slots < 0 || p->opts.cmp_slots > 4096) {
+    if (p->opts.fused_levels < 0 || p->opts.fused_levels > 10 || p->opts.cmp_slots < 0 || p->opts.cmp_slots > 4096 ||
+        p->opts.seg_slots < 0 || p->opts.seg_slots > 6144 || p->opts.seg_events < 0 || p->opts.seg_events > 4096) {
         delete p;
         return HULL3D_ERR_INVALID_ARG;
     }
@@ -319,6 +387,9 @@ int hull3d_plan_opts(hull3d_plan_t p, hull3d_opts *out)
     out->level_occupancy = p->opts.level_occupancy;
     out->cmp_level = default_cmp_level(p);
     out->cmp_slots = default_cmp_slots(p);
+    out->seg_level = default_seg_level(p);
+    out->seg_events = default_seg_events(p);
+    out->seg_slots = default_seg_slots(p);
     return HULL3D_OK;
 }
 

@@ -59,6 +59,18 @@ void launch_level(const Points &pts, int64_t n, int level, PassBufs *passes, int
 void launch_level_cmp(const Points &pts, int64_t n, int level, PassBufs *passes, int npass, int32_t *status,
                       cudaStream_t st, int scap);
 
+// Copies the movie of the last node of a level when it has no right child.
+void launch_passthrough(int64_t n, int level, int64_t lo, PassBufs *passes, int32_t *status, cudaStream_t st);
+
+struct SegBufs;
+// One level merged time-segment-parallel (K child events per window, slot
+// tables of scap points); pairs/pair_vals and their alternates hold pair_cap
+// sort items.
+void launch_seg_level(const Points &pts, int64_t n, int level, PassBufs *passes, SegBufs *sbufs, uint64_t *pairs,
+                      uint32_t *pair_vals, uint64_t *pairs_alt, uint32_t *vals_alt, unsigned long long *npairs,
+                      int *overflow, int64_t pair_cap, int64_t S_cap, int64_t M_cap, int K, int scap,
+                      const SortScratch &ss, int32_t *status, cudaStream_t st, int64_t *launches);
+
 // Faces of the root movies of both passes (level L = ceil(log2 n) in buffer L & 1):
 // orient, rotate min-first, build the sort key (f0 << 28 | f1) and value f2.
 void launch_face_keys(const Points &pts, int64_t n, int level, PassBufs *passes, uint64_t *keys, uint32_t *vals,

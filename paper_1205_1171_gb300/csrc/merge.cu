@@ -100,12 +100,15 @@ void launch_level(const Points &pts, int64_t n, int level, PassBufs *passes, int
     if (occupancy >= 4) k_level<4><<<g, 128, 0, st>>>(pts, n, level, passes[0], passes[npass - 1], status);
     else k_level<1><<<g, 128, 0, st>>>(pts, n, level, passes[0], passes[npass - 1], status);
     int64_t lo = (nodes - 1) << level;
-    if (lo + (1ll << (level - 1)) >= n) {
-        int64_t cap = 2 * (n - lo);
-        unsigned blocks = (unsigned)((cap + 255) / 256);
-        if (blocks > 1024) blocks = 1024;
-        k_passthrough<<<dim3(blocks, npass), 256, 0, st>>>(lo, level, passes[0], passes[npass - 1], status);
-    }
+    if (lo + (1ll << (level - 1)) >= n) launch_passthrough(n, level, lo, passes, status, st);
+}
+
+void launch_passthrough(int64_t n, int level, int64_t lo, PassBufs *passes, int32_t *status, cudaStream_t st)
+{
+    int64_t cap = 2 * (n - lo);
+    unsigned blocks = (unsigned)((cap + 255) / 256);
+    if (blocks > 1024) blocks = 1024;
+    k_passthrough<<<dim3(blocks, 2), 256, 0, st>>>(lo, level, passes[0], passes[1], status);
 }
 
 // ---------------------------------------------------------------------------
@@ -261,12 +264,7 @@ void launch_level_cmp(const Points &pts, int64_t n, int level, PassBufs *passes,
     k_level_cmp<<<g, CMP_THREADS, cmp_smem_bytes(scap), st>>>(pts, n, level, passes[0], passes[npass - 1], scap,
                                                               status);
     int64_t lo = (nodes - 1) << level;
-    if (lo + (1ll << (level - 1)) >= n) {
-        int64_t cap = 2 * (n - lo);
-        unsigned blocks = (unsigned)((cap + 255) / 256);
-        if (blocks > 1024) blocks = 1024;
-        k_passthrough<<<dim3(blocks, npass), 256, 0, st>>>(lo, level, passes[0], passes[npass - 1], status);
-    }
+    if (lo + (1ll << (level - 1)) >= n) launch_passthrough(n, level, lo, passes, status, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -98,32 +98,49 @@ __device__ __forceinline__ void act(LK &lk, int w)
 
 // Points are addressed by an index that is either the rank itself or a slot
 // of a compacted table; pt.rk(i) gives the rank (the perturbed x-order).
-// u0 and v0 address the ranks mid - 1 and mid.  Returns the number of parent
-// events written to `out` (at most cap); on an overflow (impossible for valid
-// input) sets *err and returns cap.
-template <class PT, class LK, class EIN, class EOUT>
-__device__ int kinetic_merge(const PT &pt, LK &lk, int u0, int v0, int mid, const EIN &L, int nl, const EIN &R,
-                             int nr, EOUT &out, int cap, bool upper, int *err)
+
+// Orientation of (p, q, r) just after the event `at` in the pass's time
+// frame (at == nullptr: t = -infinity): sign(Y~) times the sign of
+// (time(p, q, r) - time(at)), the kinetic turn Z~ - t Y~ = Y~ (t_pqr - t).
+template <class PT>
+__device__ __forceinline__ int turn_after(const PT &pt, int p, int q, int r, const Tri *at, bool upper)
 {
-    // 1. bridge at t = -inf; u only moves left and v only right, so this ends
-    int u = u0, v = v0;
+    if (!at) return turn3(pt, p, q, r);
+    Tri t;
+    tri_make(pt, t, p, q, r);
+    return tri_cmp(pt, t, *at, upper) > 0 ? t.s : -t.s;
+}
+
+// The bridge of the two child hulls just after `at`: walks in from the inner
+// x-extremes u (left) and v (right); u only moves left and v only right.
+template <class PT, class LK>
+__device__ void bridge_walk(const PT &pt, const LK &lk, int &u, int &v, const Tri *at, bool upper)
+{
     for (;;) {
         int vn = lk.nxt(v);
-        if (vn != NIL && turn3(pt, u, v, vn) < 0) { v = vn; continue; }
+        if (vn != NIL && turn_after(pt, u, v, vn, at, upper) < 0) { v = vn; continue; }
         int up = lk.prv(u);
-        if (up != NIL && turn3(pt, up, u, v) < 0) { u = up; continue; }
+        if (up != NIL && turn_after(pt, up, u, v, at, upper) < 0) { u = up; continue; }
         break;
     }
+}
 
-    // 2. forward pass
+// Forward pass (step 2) from the bridge (u, v), after the event `old` when
+// have_old.  Consumes the child movies (L, nl) and (R, nr) and appends the
+// visible events to `out`.  With stop_at_end it stops once both child movies
+// are consumed (a time window that does not reach t = +infinity).  Returns
+// the number of events written; u and v are left at the final bridge.
+template <class PT, class LK, class EIN, class EOUT>
+__device__ int kinetic_forward(const PT &pt, LK &lk, int &u, int &v, Tri old, bool have_old, const EIN &L, int nl,
+                               const EIN &R, int nr, EOUT &out, int cap, bool upper, bool stop_at_end, int *err)
+{
     Tri c[6];
     unsigned valid = 0;  // bit l: candidate l is finite and later than the last event
 #pragma unroll
     for (int l = 0; l < 6; l++) { c[l].p = c[l].q = c[l].r = -2; c[l].s = 0; }
-    Tri old;
-    bool have_old = false;
     int i = 0, j = 0, k = 0;
     for (;;) {
+        if (stop_at_end && i >= nl && j >= nr) break;
         const int e0 = i < nl ? (int)(L.w(i) & RANK_MASK) : NIL;
         const int e1 = j < nr ? (int)(R.w(j) & RANK_MASK) : NIL;
         const int2 l0 = e0 >= 0 ? lk.get(e0) : make_int2(NIL, NIL);
@@ -177,8 +194,15 @@ __device__ int kinetic_merge(const PT &pt, LK &lk, int u0, int v0, int mid, cons
         have_old = true;
         valid &= ~(1u << best);
     }
+    return k;
+}
 
-    // 3. backward pass from the t = +inf bridge
+// Backward pass (step 3): from the t = +infinity bridge (u, v) undo the
+// parent's k events in reverse, leaving the parent's t = -infinity hull and
+// the event-time links of its event points.
+template <class PT, class LK, class EOUT>
+__device__ void kinetic_backward(const PT &pt, LK &lk, int u, int v, int mid, const EOUT &out, int k)
+{
     lk.set_nxt(u, v);
     lk.set_prv(v, u);
     for (int kk = k - 1; kk >= 0; kk--) {
@@ -195,6 +219,23 @@ __device__ int kinetic_merge(const PT &pt, LK &lk, int u0, int v0, int mid, cons
             if (rw < mid) u = w; else v = w;
         }
     }
+}
+
+// The whole merge of one node.  u0 and v0 address the ranks mid - 1 and mid.
+// Returns the number of parent events written to `out` (at most cap); on an
+// overflow (impossible for valid input) sets *err and returns cap.
+template <class PT, class LK, class EIN, class EOUT>
+__device__ int kinetic_merge(const PT &pt, LK &lk, int u0, int v0, int mid, const EIN &L, int nl, const EIN &R,
+                             int nr, EOUT &out, int cap, bool upper, int *err)
+{
+    int u = u0, v = v0;
+    bridge_walk(pt, lk, u, v, (const Tri *)nullptr, upper);  // 1. bridge at t = -inf
+    Tri none;
+    none.p = none.q = none.r = -2;
+    none.s = 0;
+    int k = kinetic_forward(pt, lk, u, v, none, false, L, nl, R, nr, out, cap, upper, false, err);  // 2.
+    if (k >= cap && *err) return k;
+    kinetic_backward(pt, lk, u, v, mid, out, k);  // 3.
     return k;
 }
 

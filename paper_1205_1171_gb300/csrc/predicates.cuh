@@ -58,7 +58,7 @@ __device__ __forceinline__ void zy3(const P3 &p, const P3 &q, const P3 &r, long 
 }
 
 // sign of Y~(p, q, r): nonzero for distinct points.
-__device__ __noinline__ int turn_slow(const P3 &p, const P3 &q, const P3 &r)
+static __device__ __noinline__ int turn_slow(const P3 &p, const P3 &q, const P3 &r)
 {
     long long nx, ny, nz;
     normal3(p, q, r, nx, ny, nz);

@@ -1,0 +1,473 @@
+// segmerge.cu -- kernels of the time-segment-parallel merge (see segmerge.cuh).
+#include "internal.h"
+#include "segmerge.cuh"
+
+namespace hull3d {
+
+__device__ __forceinline__ void seg_status(int32_t *status, int code) { atomicCAS(status, 0, code); }
+
+struct SegArgs {
+    Points pts;
+    SegGeom geo;
+    PassBufs pb[2];
+    SegBufs sb[2];
+    uint64_t *pairs;                 // keys; sorted in place between the kernels
+    uint32_t *pair_vals;
+    unsigned long long *npairs;
+    int *overflow;
+    int64_t S_cap, M_cap;
+    int32_t *status;
+};
+
+// ---- bounds: one thread per (merge, window) --------------------------------
+__global__ void k_seg_bounds(SegArgs a)
+{
+    if (*a.status) return;
+    const int pass = blockIdx.y;
+    const SegGeom &G = a.geo;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t m = t / G.smax;
+    const int s = (int)(t % G.smax);
+    const int64_t half = 1ll << (G.level - 1);
+    const int64_t lo = m << G.level;
+    if (lo >= G.n) return;
+    const int64_t mid = lo + half, hi = (lo + 2 * half < G.n) ? lo + 2 * half : G.n;
+    if (mid >= hi) return;
+    const PassBufs &pb = a.pb[pass];
+    const SegBufs &sb = a.sb[pass];
+    const int src = (G.level - 1) & 1;
+    const int nl = pb.cnt[src][lo], nr = pb.cnt[src][mid];
+    const int S = seg_count(nl, nr, G.K, G.smax);
+    if (s == 0) { sb.nseg[m] = S; sb.nofit[m] = 0; }
+    if (s >= S) return;
+    const int64_t g = m * G.smax + s;
+    int kL = 0;
+    const int j = (int)(((int64_t)s * (nl + nr)) / S);
+    if (s > 0) {
+        GPts gp{ a.pts.P };
+        const unsigned *W = pb.W[src];
+        const int *A = pb.A[src], *B = pb.B[src];
+        kL = merge_path(gp, W + 2 * lo, A + 2 * lo, B + 2 * lo, nl, W + 2 * mid, A + 2 * mid, B + 2 * mid, nr, j,
+                        pass != 0);
+    }
+    sb.bound[g] = make_int2(kL, j - kL);
+    // the x-extremes of both children are on their hulls at every time
+    int ext[4] = { (int)lo, (int)mid - 1, (int)mid, (int)hi - 1 };
+    int cnt = 2 + (ext[1] != ext[0]) + (ext[3] != ext[2]);
+    unsigned long long pos = atomicAdd(a.npairs, (unsigned long long)cnt);
+    if (pos + cnt > (unsigned long long)G.pair_cap) { atomicExch(a.overflow, 1); return; }
+    a.pairs[pos++] = seg_key(pass, g, 0, ext[0], a.S_cap);
+    if (ext[1] != ext[0]) a.pairs[pos++] = seg_key(pass, g, 0, ext[1], a.S_cap);
+    a.pairs[pos++] = seg_key(pass, g, 1, ext[2], a.S_cap);
+    if (ext[3] != ext[2]) a.pairs[pos++] = seg_key(pass, g, 1, ext[3], a.S_cap);
+}
+
+// Maps a position q of the level's source movie buffer to its child movie:
+// returns false when q holds no event of a merged child.
+__device__ __forceinline__ bool seg_locate(const SegGeom &G, const PassBufs &pb, int64_t q, int64_t &clo, int64_t &plo,
+                                           int &k, int &E)
+{
+    const int64_t half = 1ll << (G.level - 1);
+    const int64_t r = q >> 1;
+    if (r >= G.n) return false;
+    clo = r & ~(half - 1);
+    plo = r & ~(2 * half - 1);
+    const int64_t pmid = plo + half, phi = (plo + 2 * half < G.n) ? plo + 2 * half : G.n;
+    if (pmid >= phi) return false;  // pass-through node
+    k = (int)(q - 2 * clo);
+    E = pb.cnt[(G.level - 1) & 1][clo];
+    return k < E;
+}
+
+// ---- idx: every event records its index under its point --------------------
+__global__ void k_seg_idx(SegArgs a)
+{
+    if (*a.status) return;
+    const int pass = blockIdx.y;
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t clo, plo;
+    int k, E;
+    if (!seg_locate(a.geo, a.pb[pass], q, clo, plo, k, E)) return;
+    const unsigned w = a.pb[pass].W[(a.geo.level - 1) & 1][q];
+    const int rk = (int)(w & RANK_MASK);
+    if (w & INS_BIT) a.sb[pass].ins_idx[rk] = k;
+    else a.sb[pass].del_idx[rk] = k;
+}
+
+// ---- pairs: each event point joins the start hulls of the windows it spans --
+__global__ void k_seg_pairs(SegArgs a)
+{
+    if (*a.status) return;
+    const int pass = blockIdx.y;
+    const SegGeom &G = a.geo;
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t clo, plo;
+    int k, E;
+    const PassBufs &pb = a.pb[pass];
+    const SegBufs &sb = a.sb[pass];
+    if (!seg_locate(G, pb, q, clo, plo, k, E)) return;
+    const unsigned *CW = pb.W[(G.level - 1) & 1] + 2 * clo;
+    const unsigned w = CW[k];
+    const int rk = (int)(w & RANK_MASK);
+    int lo_p, hi_p;  // alive after i child events iff lo_p < i <= hi_p
+    if (w & INS_BIT) {
+        lo_p = k;
+        const int dd = sb.del_idx[rk];
+        hi_p = (dd > k && dd < E && (int)(CW[dd] & RANK_MASK) == rk && !(CW[dd] & INS_BIT)) ? dd : E;
+    } else {
+        const int ii = sb.ins_idx[rk];
+        if (ii >= 0 && ii < k && (int)(CW[ii] & RANK_MASK) == rk && (CW[ii] & INS_BIT)) return;  // counted at its insert
+        lo_p = -1;
+        hi_p = k;
+    }
+    const int child = clo == plo ? 0 : 1;
+    const int64_t m = plo >> G.level;
+    const int S = sb.nseg[m];
+    const int2 *bd = sb.bound + m * G.smax;
+    // windows s with lo_p < kC_s <= hi_p (kC_s is nondecreasing in s)
+    int b0 = 0, b1 = S;
+    while (b0 < b1) {
+        int c = (b0 + b1) >> 1;
+        int kc = child ? bd[c].y : bd[c].x;
+        if (kc > lo_p) b1 = c; else b0 = c + 1;
+    }
+    const int s_first = b0;
+    b0 = s_first; b1 = S;
+    while (b0 < b1) {
+        int c = (b0 + b1) >> 1;
+        int kc = child ? bd[c].y : bd[c].x;
+        if (kc <= hi_p) b0 = c + 1; else b1 = c;
+    }
+    const int cnt = b0 - s_first;
+    if (cnt <= 0) return;
+    unsigned long long pos = atomicAdd(a.npairs, (unsigned long long)cnt);
+    if (pos + cnt > (unsigned long long)G.pair_cap) { atomicExch(a.overflow, 1); return; }
+    for (int s = s_first; s < s_first + cnt; s++) a.pairs[pos++] = seg_key(pass, m * G.smax + s, child, rk, a.S_cap);
+}
+
+// ---- merge: one warp per window ---------------------------------------------
+struct SegOut {  // slots in, ranks out
+    unsigned *W;
+    int *A, *B;
+    const int *RK;
+    __device__ __forceinline__ void put(int k, unsigned w, int a, int b)
+    {
+        W[k] = (unsigned)RK[w & RANK_MASK] | (w & INS_BIT);
+        A[k] = RK[a];
+        B[k] = RK[b];
+    }
+};
+
+struct SegIn {
+    const unsigned *W;
+    __device__ __forceinline__ unsigned w(int i) const { return W[i]; }
+};
+
+constexpr int SEG_THREADS = 32;
+
+// first index in [0, cnt) of keys >= key
+__device__ __forceinline__ int64_t lower_key(const uint64_t *keys, int64_t cnt, uint64_t key)
+{
+    int64_t lo = 0, hi = cnt;
+    while (lo < hi) {
+        int64_t m = (lo + hi) >> 1;
+        if (keys[m] < key) lo = m + 1; else hi = m;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(SEG_THREADS) k_seg_merge(SegArgs a)
+{
+    extern __shared__ int sm[];
+    __shared__ int s_bad, s_nins;
+    if (*a.status) return;
+    const int pass = blockIdx.y;
+    const bool upper = pass != 0;
+    const SegGeom &G = a.geo;
+    const int64_t g = blockIdx.x;
+    const int64_t m = g / G.smax;
+    const int s = (int)(g % G.smax);
+    const int64_t half = 1ll << (G.level - 1);
+    const int64_t lo = m << G.level;
+    if (lo >= G.n) return;
+    const int64_t mid = lo + half, hi = (lo + 2 * half < G.n) ? lo + 2 * half : G.n;
+    if (mid >= hi) return;
+    const PassBufs &pb = a.pb[pass];
+    const SegBufs &sb = a.sb[pass];
+    const int S = sb.nseg[m];
+    if (s >= S) return;
+    if (*a.overflow) { if (threadIdx.x == 0) sb.nofit[m] = 1; return; }
+    const int tid = threadIdx.x;
+    const int src = (G.level - 1) & 1;
+    const int nl = pb.cnt[src][lo], nr = pb.cnt[src][mid];
+    const int2 b0 = sb.bound[g];
+    const int2 b1 = (s + 1 < S) ? sb.bound[g + 1] : make_int2(nl, nr);
+    const unsigned *LW = pb.W[src] + 2 * lo, *RW = pb.W[src] + 2 * mid;
+    const int wl = b1.x - b0.x, wr = b1.y - b0.y;
+    // start hulls
+    const int64_t np = (int64_t)*a.npairs;
+    const int64_t aL0 = lower_key(a.pairs, np, seg_key(pass, g, 0, 0, a.S_cap));
+    const int64_t aR0 = lower_key(a.pairs, np, seg_key(pass, g, 1, 0, a.S_cap));
+    const int64_t aR1 = lower_key(a.pairs, np, seg_key(pass, g + 1, 0, 0, a.S_cap));
+    const int aL = (int)(aR0 - aL0), aR = (int)(aR1 - aR0);
+    // inserted points of the window
+    if (tid == 0) { s_bad = 0; s_nins = 0; }
+    __syncthreads();
+    int nins_local = 0;
+    for (int e = tid; e < wl + wr; e += SEG_THREADS) {
+        unsigned w = e < wl ? LW[b0.x + e] : RW[b0.y + e - wl];
+        nins_local += (w & INS_BIT) ? 1 : 0;
+    }
+    atomicAdd(&s_nins, nins_local);
+    __syncthreads();
+    const int nins = s_nins;
+    const int base_ins = aL + aR;
+    const int tsize = base_ins + nins + 3;  // + the three points of the window's boundary event
+    if (tsize > G.scap || wl + wr > G.K + 1 || aL < 1 || aR < 1) {
+        if (tid == 0) sb.nofit[m] = 1;
+        return;
+    }
+    int4 *sPt = (int4 *)sm;
+    int2 *sLk = (int2 *)(sPt + G.scap);
+    int *sRK = (int *)(sLk + G.scap);
+    unsigned *sIn = (unsigned *)(sRK + G.scap);  // window movies as slots: left then right
+    // start hulls, linked in x-order
+    for (int i = tid; i < aL + aR; i += SEG_THREADS) {
+        const bool left = i < aL;
+        const int r = (int)(a.pairs[aL0 + i] & ((1ull << 28) - 1));
+        sRK[i] = r;
+        sPt[i] = a.pts.P[r];
+        const int first = left ? 0 : aL, last = left ? aL - 1 : aL + aR - 1;
+        sLk[i] = make_int2(i > first ? i - 1 : NIL, i < last ? i + 1 : NIL);
+    }
+    // slots of the inserted points, in window order (warp prefix over ballots)
+    {
+        int run = 0;
+        for (int e0 = 0; e0 < wl + wr; e0 += SEG_THREADS) {
+            const int e = e0 + tid;
+            unsigned w = 0;
+            if (e < wl + wr) w = e < wl ? LW[b0.x + e] : RW[b0.y + e - wl];
+            const bool ins = e < wl + wr && (w & INS_BIT);
+            const unsigned bal = __ballot_sync(0xffffffffu, ins);
+            if (ins) {
+                const int slot = base_ins + run + __popc(bal & ((1u << tid) - 1u));
+                const int r = (int)(w & RANK_MASK);
+                sRK[slot] = r;
+                sPt[slot] = a.pts.P[r];
+                sb.smap[r] = slot;
+            }
+            run += __popc(bal);
+        }
+    }
+    __syncthreads();
+    // rank -> slot: binary search in the child's start hull, else an inserted point
+    auto find = [&](int r, int child) -> int {
+        if (r < 0) return NIL;
+        int f = child ? aL : 0, l = child ? aL + aR : aL;
+        while (f < l) {
+            int c = (f + l) >> 1;
+            if (sRK[c] < r) f = c + 1; else l = c;
+        }
+        if (f < (child ? aL + aR : aL) && sRK[f] == r) return f;
+        const int sl = sb.smap[r];
+        if (sl >= base_ins && sl < base_ins + nins && sRK[sl] == r) return sl;
+        s_bad = 1;
+        return NIL;
+    };
+    for (int i = tid; i < nins; i += SEG_THREADS) {
+        const int slot = base_ins + i;
+        const int r = sRK[slot];
+        const int child = r >= (int)mid ? 1 : 0;
+        const int2 l = pb.lk[r];  // neighbours at its insertion
+        sLk[slot] = make_int2(find(l.x, child), find(l.y, child));
+    }
+    for (int e = tid; e < wl + wr; e += SEG_THREADS) {
+        const bool left = e < wl;
+        const unsigned w = left ? LW[b0.x + e] : RW[b0.y + e - wl];
+        sIn[e] = (unsigned)find((int)(w & RANK_MASK), left ? 0 : 1) | (w & INS_BIT);
+    }
+    __syncthreads();
+    if (tid == 0 && !s_bad) {
+        CPts cp{ sPt, sRK };
+        CLinks lk{ sLk };
+        Tri at;
+        at.s = 0;
+        if (s > 0) {  // the window starts just after the latest child event before it
+            GPts gp{ a.pts.P };
+            const int *A = pb.A[src], *B = pb.B[src];
+            int eb = -1;  // global index of that event in the source buffer
+            if (b0.x > 0 && b0.y > 0) {
+                Tri tl, tr;
+                ev_tri(gp, pb.W[src], A, B, (int)(2 * lo) + b0.x - 1, tl);
+                ev_tri(gp, pb.W[src], A, B, (int)(2 * mid) + b0.y - 1, tr);
+                eb = tri_cmp(gp, tl, tr, upper) > 0 ? (int)(2 * lo) + b0.x - 1 : (int)(2 * mid) + b0.y - 1;
+            } else {
+                eb = b0.x > 0 ? (int)(2 * lo) + b0.x - 1 : (int)(2 * mid) + b0.y - 1;
+            }
+            const int tb = base_ins + nins;
+            const int rr[3] = { A[eb], (int)(pb.W[src][eb] & RANK_MASK), B[eb] };
+            for (int q = 0; q < 3; q++) {
+                sRK[tb + q] = rr[q];
+                sPt[tb + q] = a.pts.P[rr[q]];
+                sLk[tb + q] = make_int2(NIL, NIL);
+            }
+            tri_make(cp, at, tb, tb + 1, tb + 2);
+        }
+        int u = aL - 1, v = aL;  // the inner x-extremes mid - 1 and mid
+        bridge_walk(cp, lk, u, v, s > 0 ? &at : (const Tri *)nullptr, upper);
+        if (s == 0) sb.bridge0[m] = make_int2(sRK[u], sRK[v]);
+        SegIn L{ sIn }, R{ sIn + wl };
+        SegOut out{ sb.oW + g * G.ocap, sb.oA + g * G.ocap, sb.oB + g * G.ocap, sRK };
+        int err = 0;
+        int k = kinetic_forward(cp, lk, u, v, at, s > 0, L, wl, R, wr, out, G.ocap, upper, s + 1 < S, &err);
+        sb.ocnt[g] = k;
+        if (err) s_bad = 1;
+    }
+    __syncthreads();
+    if (tid == 0 && s_bad) sb.nofit[m] = 1;
+}
+
+// ---- concat: one CTA per merge ------------------------------------------------
+constexpr int CAT_THREADS = 256;
+
+__global__ void __launch_bounds__(CAT_THREADS) k_seg_concat(SegArgs a)
+{
+    __shared__ int s_off[CAT_THREADS + 1];
+    if (*a.status) return;
+    const int pass = blockIdx.y;
+    const SegGeom &G = a.geo;
+    const int64_t m = blockIdx.x;
+    const int64_t half = 1ll << (G.level - 1);
+    const int64_t lo = m << G.level;
+    if (lo >= G.n) return;
+    const int64_t mid = lo + half, hi = (lo + 2 * half < G.n) ? lo + 2 * half : G.n;
+    if (mid >= hi) return;
+    const PassBufs &pb = a.pb[pass];
+    const SegBufs &sb = a.sb[pass];
+    if (sb.nofit[m]) return;  // merged serially by k_seg_fallback
+    const int dst = G.level & 1;
+    const int S = sb.nseg[m];
+    unsigned *W = pb.W[dst] + 2 * lo;
+    int *A = pb.A[dst] + 2 * lo, *B = pb.B[dst] + 2 * lo;
+    int base = 0;
+    for (int s0 = 0; s0 < S; s0 += CAT_THREADS) {
+        // exclusive scan of this chunk's window counts
+        const int s = s0 + threadIdx.x;
+        const int c = s < S ? sb.ocnt[m * G.smax + s] : 0;
+        s_off[threadIdx.x + 1] = c;
+        if (threadIdx.x == 0) s_off[0] = 0;
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int t = 1; t <= CAT_THREADS; t++) s_off[t] += s_off[t - 1];
+        __syncthreads();
+        const int chunk = min(CAT_THREADS, S - s0);
+        for (int t = 0; t < chunk; t++) {
+            const int64_t g = m * G.smax + s0 + t;
+            const int off = base + s_off[t];
+            const int cnt = s_off[t + 1] - s_off[t];
+            for (int e = threadIdx.x; e < cnt; e += CAT_THREADS) {
+                const unsigned w = sb.oW[g * G.ocap + e];
+                const int aa = sb.oA[g * G.ocap + e], bb = sb.oB[g * G.ocap + e];
+                W[off + e] = w;
+                A[off + e] = aa;
+                B[off + e] = bb;
+                if (w & INS_BIT) pb.lk[w & RANK_MASK] = make_int2(aa, bb);  // event-time links of an insertion
+            }
+        }
+        base += s_off[chunk];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        pb.cnt[dst][lo] = base;
+        const int2 br = sb.bridge0[m];  // join the two t = -inf hulls
+        pb.lk[br.x].y = br.y;
+        pb.lk[br.y].x = br.x;
+        atomicAdd(pb.lev_events + G.level, (unsigned long long)base);
+    }
+}
+
+// ---- fallback: serial merge of the merges that did not fit -------------------
+__global__ void k_seg_fallback(SegArgs a)
+{
+    if (*a.status) return;
+    const int pass = blockIdx.y;
+    const SegGeom &G = a.geo;
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t half = 1ll << (G.level - 1);
+    const int64_t lo = m << G.level;
+    if (lo >= G.n) return;
+    const int64_t mid = lo + half, hi = (lo + 2 * half < G.n) ? lo + 2 * half : G.n;
+    if (mid >= hi) return;
+    const PassBufs &pb = a.pb[pass];
+    if (!a.sb[pass].nofit[m]) return;
+    const int src = (G.level - 1) & 1, dst = G.level & 1;
+    GPts gp{ a.pts.P };
+    GLinks lk{ pb.lk };
+    GEvIn L{ pb.W[src] + 2 * lo }, R{ pb.W[src] + 2 * mid };
+    GEvOut out{ pb.W[dst] + 2 * lo, pb.A[dst] + 2 * lo, pb.B[dst] + 2 * lo };
+    int err = 0;
+    int k = kinetic_merge(gp, lk, (int)mid - 1, (int)mid, (int)mid, L, pb.cnt[src][lo], R, pb.cnt[src][mid], out,
+                          (int)(2 * (hi - lo)), pass != 0, &err);
+    pb.cnt[dst][lo] = k;
+    if (err) seg_status(a.status, HULL3D_ERR_INTERNAL);
+    atomicAdd(pb.lev_events + G.level, (unsigned long long)k);
+}
+
+size_t seg_smem_bytes(int scap, int K) { return (size_t)scap * (sizeof(int4) + sizeof(int2) + sizeof(int)) + 4 * (K + 1); }
+
+void launch_seg_level(const Points &pts, int64_t n, int level, PassBufs *passes, SegBufs *sbufs, uint64_t *pairs,
+                      uint32_t *pair_vals, uint64_t *pairs_alt, uint32_t *vals_alt, unsigned long long *npairs,
+                      int *overflow, int64_t pair_cap, int64_t S_cap, int64_t M_cap, int K, int scap,
+                      const SortScratch &ss, int32_t *status, cudaStream_t st, int64_t *launches)
+{
+    SegArgs a;
+    a.pts = pts;
+    a.geo.n = n;
+    a.geo.level = level;
+    a.geo.K = K;
+    a.geo.smax = (int)(((1ll << (level + 1)) + K - 1) / K);
+    a.geo.scap = scap;
+    a.geo.ocap = 2 * K + 256;
+    a.geo.pair_cap = pair_cap;
+    a.pb[0] = passes[0];
+    a.pb[1] = passes[1];
+    a.sb[0] = sbufs[0];
+    a.sb[1] = sbufs[1];
+    a.npairs = npairs;
+    a.overflow = overflow;
+    a.S_cap = S_cap;
+    a.M_cap = M_cap;
+    a.status = status;
+    const int64_t M = (n + (1ll << level) - 1) >> level;
+    const int64_t G = M * a.geo.smax;
+    cudaMemsetAsync(npairs, 0, sizeof(unsigned long long), st);
+    cudaMemsetAsync(overflow, 0, sizeof(int), st);
+    a.pairs = pairs;
+    a.pair_vals = pair_vals;
+    k_seg_bounds<<<dim3((unsigned)((G + 127) / 128), 2), 128, 0, st>>>(a);
+    k_seg_idx<<<dim3((unsigned)((2 * n + 255) / 256), 2), 256, 0, st>>>(a);
+    k_seg_pairs<<<dim3((unsigned)((2 * n + 255) / 256), 2), 256, 0, st>>>(a);
+    *launches += 3;
+    int key_bits = 28;
+    while ((1ll << (key_bits - 28)) < 4 * S_cap) key_bits++;
+    int which = radix_sort_pairs(pairs, pair_vals, pairs_alt, vals_alt, pair_cap, (const int64_t *)npairs, key_bits, ss,
+                                 st, launches);
+    a.pairs = which ? pairs_alt : pairs;
+    a.pair_vals = which ? vals_alt : pair_vals;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_seg_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    k_seg_merge<<<dim3((unsigned)G, 2), SEG_THREADS, seg_smem_bytes(scap, K), st>>>(a);
+    k_seg_concat<<<dim3((unsigned)M, 2), CAT_THREADS, 0, st>>>(a);
+    k_seg_fallback<<<dim3((unsigned)((M + 31) / 32), 2), 32, 0, st>>>(a);
+    *launches += 3;
+    const int64_t last_lo = (M - 1) << level;
+    if (last_lo + (1ll << (level - 1)) >= n) {
+        launch_passthrough(n, level, last_lo, passes, status, st);
+        *launches += 1;
+    }
+}
+
+}  // namespace hull3d

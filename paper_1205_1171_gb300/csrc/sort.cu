@@ -62,7 +62,13 @@ constexpr int RS_THREADS = 256;
 constexpr int RS_ITEMS = SORT_TILE / RS_THREADS;  // 16
 constexpr int RS_WARPS = RS_THREADS / 32;
 
-__device__ __forceinline__ int64_t count_of(int64_t n, const int64_t *d_n) { return d_n ? *d_n : n; }
+// items to sort: the capacity n, or a device count clamped to it
+__device__ __forceinline__ int64_t count_of(int64_t n, const int64_t *d_n)
+{
+    if (!d_n) return n;
+    int64_t c = *d_n;
+    return c < n ? c : n;
+}
 
 __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t *__restrict__ keys, int64_t n,
                                                         const int64_t *d_n, int shift, uint32_t *hist, int64_t T)

@@ -47,10 +47,12 @@ class Hull3DError(RuntimeError):
         self.code = code
 
 
+OPT_NAMES = ("fused_levels", "seg_level", "seg_events", "use_graph", "level_occupancy", "cmp_level", "cmp_slots",
+             "seg_slots")
+
+
 class Opts(ctypes.Structure):
-    _fields_ = [("fused_levels", ctypes.c_int32), ("seg_level", ctypes.c_int32), ("seg_events", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("level_occupancy", ctypes.c_int32), ("cmp_level", ctypes.c_int32),
-                ("cmp_slots", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+    _fields_ = [(k, ctypes.c_int32) for k in OPT_NAMES] + [("reserved", ctypes.c_int32 * 8)]
 
 
 def load():
@@ -123,11 +125,13 @@ def max_faces(n: int) -> int:
 class Hull3D:
     """A plan: scratch for hulls of up to max_n points (and batches totalling max_n)."""
 
-    def __init__(self, max_n: int, max_clouds: int = 0, fused_levels: int = 0, seg_level: int = 0,
-                 seg_events: int = 0, use_graph: int = 0, level_occupancy: int = 0, cmp_level: int = 0,
-                 cmp_slots: int = 0):
+    def __init__(self, max_n: int, max_clouds: int = 0, **knobs):
+        """knobs: any of OPT_NAMES (0 = automatic)."""
         self._lib = load()
-        opts = Opts(fused_levels, seg_level, seg_events, use_graph, level_occupancy, cmp_level, cmp_slots)
+        bad = set(knobs) - set(OPT_NAMES)
+        if bad:
+            raise TypeError(f"unknown options {sorted(bad)}")
+        opts = Opts(*[int(knobs.get(k, 0)) for k in OPT_NAMES])
         plan = ctypes.c_void_p()
         rc = self._lib.hull3d_plan(ctypes.byref(plan), int(max_n), int(max_clouds), ctypes.byref(opts))
         if rc:

@@ -78,6 +78,23 @@ def test_upper_level_kernels_agree(H, cmp_level, cmp_slots):
         p.close()
 
 
+@pytest.mark.parametrize("seg_level,seg_events,seg_slots", [(2, 4, 64), (3, 16, 256), (6, 64, 2048), (9, 512, 2048),
+                                                            (4, 32, 40)])
+def test_segment_parallel_levels_agree(H, seg_level, seg_events, seg_slots):
+    """Time-segment-parallel top levels (many windows per merge; tiny slot tables
+    force the serial fallback) give the oracle's faces."""
+    p = H.Hull3D(1 << 15, seg_level=seg_level, seg_events=seg_events, seg_slots=seg_slots)
+    try:
+        for dist in inputs.DISTS:
+            for n in (3, 5, 77, 1000, 1 << 15):
+                pts = inputs.cloud_seeded(dist, n, 5100 + n + seg_level)
+                assert np.array_equal(run(p, pts), oracle.hull(pts)), (dist, n)
+        for pts in _tiny_sets(100, 23):
+            assert np.array_equal(run(p, pts), oracle.hull(pts)), pts.tolist()
+    finally:
+        p.close()
+
+
 def test_config_small_cube_4096(plan):
     pts = inputs.cloud_seeded("cube", 4096, inputs.seed_for(1))
     got = run(plan, pts)
