@@ -49,6 +49,7 @@ extern "C" {
 #define HULL3D_ERR_DEVICE_TIMEOUT 7 /* a bounded device wait ran out */
 #define HULL3D_ERR_CUDA 8          /* a CUDA runtime call failed (see hull3d_last_cuda_error) */
 #define HULL3D_ERR_INTERNAL 9      /* an internal consistency check failed */
+#define HULL3D_ERR_TOO_LARGE 10    /* n above HULL3D_STATIC_MAX_N (hull3d_compute_static only) */
 
 #define HULL3D_MAX_N (1 << 28)     /* largest n one plan accepts */
 
@@ -122,6 +123,35 @@ int hull3d_compute_host(hull3d_plan_t plan, const int32_t *h_xyz, int64_t n, int
 int hull3d_batch_async(hull3d_plan_t plan, const int32_t *d_xyz, const int64_t *h_offsets, int64_t B,
                        int32_t *d_faces, const int64_t *h_face_offsets, int64_t *d_nfaces, int32_t *d_status,
                        void *stream);
+
+/* Allocation-free form of hull3d_compute_async, for hulls of at most
+ * HULL3D_STATIC_MAX_N points.  The paper has no counterpart: this is a
+ * convenience of this library.
+ *
+ * It exists for callers that may not allocate device memory themselves:
+ * code running inside a host framework that owns every byte of the device
+ * (a fixed memory pool or a budget it must not exceed), and latency-critical
+ * loops that cannot afford cudaMalloc/cudaFree, which may synchronise the
+ * device.  Such callers pass their own input and output buffers; all
+ * scratch comes from one static device array of HULL3D_STATIC_SCRATCH_BYTES
+ * that this library defines, so every GPU that loads the library holds that
+ * array until the process exits.  This entry point calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *
+ *   d_xyz, n, d_faces, cap_faces, d_nfaces, d_status, stream: as for
+ *   hull3d_compute_async (d_nfaces and d_status may not be NULL here).
+ *   n > HULL3D_STATIC_MAX_N returns HULL3D_ERR_TOO_LARGE and enqueues nothing.
+ *
+ * The first call on a device looks up the device address of the static array
+ * (with that device current); make that first call before any stream capture.
+ * All calls share the one array: calls whose work may overlap on the GPU
+ * (different streams, or different host threads) race and must be serialised
+ * by the caller.  Every value the pipeline needs to start from zero is
+ * cleared by each call, so the contents left by an earlier call do not matter. */
+#define HULL3D_STATIC_MAX_N 16384
+#define HULL3D_STATIC_SCRATCH_BYTES (4 << 20)
+int hull3d_compute_static(const int32_t *d_xyz, int64_t n, int32_t *d_faces, int64_t cap_faces, int64_t *d_nfaces,
+                          int32_t *d_status, void *stream);
 
 /* Text for a HULL3D_* code. */
 const char *hull3d_strerror(int code);

@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -519,6 +520,64 @@ int hull3d_level_events(hull3d_plan_t p, int64_t *out)
     return HULL3D_OK;
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point: the pipeline's scratch lives in one static
+// device array (held by every GPU that loads the library until exit).
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_static_scratch[HULL3D_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+hull3d_plan_s g_static_plan[kMaxDevices];
+bool g_static_ready[kMaxDevices] = {};
+
+// Once per device, with that device current: look up the array's device
+// address (in host code its name is only a host-side stand-in) and lay the
+// plan's buffers out in it.
+int static_plan_for_current_device(hull3d_plan_s **out)
+{
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return HULL3D_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    hull3d_plan_s *p = &g_static_plan[dev];
+    if (!g_static_ready[dev]) {
+        void *base = nullptr;
+        CK(cudaGetSymbolAddress(&base, g_static_scratch));
+        p->max_n = HULL3D_STATIC_MAX_N;
+        p->max_clouds = 0;
+        p->device = dev;
+        p->opts.seg_level = 64;  // n <= 2^14: no time-segment-parallel levels, no window scratch
+        if (layout(p, nullptr) > (size_t)HULL3D_STATIC_SCRATCH_BYTES) return HULL3D_ERR_INTERNAL;
+        p->pool = (char *)base;
+        p->pool_bytes = layout(p, p->pool);
+        g_static_ready[dev] = true;
+    }
+    *out = p;
+    return HULL3D_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hull3d_compute_static(const int32_t *d_xyz, int64_t n, int32_t *d_faces, int64_t cap_faces, int64_t *d_nfaces,
+                          int32_t *d_status, void *stream)
+{
+    if (!d_xyz || !d_nfaces || !d_status || n < 1) return HULL3D_ERR_INVALID_ARG;
+    if (n > HULL3D_STATIC_MAX_N) return HULL3D_ERR_TOO_LARGE;
+    if (n >= 3 && (!d_faces)) return HULL3D_ERR_INVALID_ARG;
+    if (n >= 3 && cap_faces < 2 * n - 4) return HULL3D_ERR_CAPACITY;
+    hull3d_plan_s *p = nullptr;
+    int rc = static_plan_for_current_device(&p);
+    if (rc) return rc;
+    return enqueue_hull(p, d_xyz, n, d_faces, d_nfaces, d_status, (cudaStream_t)stream);
+}
+
 const char *hull3d_strerror(int code)
 {
     switch (code) {
@@ -532,6 +591,7 @@ const char *hull3d_strerror(int code)
     case HULL3D_ERR_DEVICE_TIMEOUT: return "a bounded device wait ran out";
     case HULL3D_ERR_CUDA: return "CUDA runtime error";
     case HULL3D_ERR_INTERNAL: return "internal consistency check failed";
+    case HULL3D_ERR_TOO_LARGE: return "n above HULL3D_STATIC_MAX_N for the allocation-free entry point";
     default: return "unknown error";
     }
 }

@@ -27,12 +27,14 @@ ERR_BUDGET = 6
 ERR_DEVICE_TIMEOUT = 7
 ERR_CUDA = 8
 ERR_INTERNAL = 9
+ERR_TOO_LARGE = 10
+STATIC_MAX_N = 16384
 
 # every symbol include/hull3d.h declares
 EXPORTS = (
     "hull3d_plan", "hull3d_plan_opts", "hull3d_destroy", "hull3d_plan_bytes", "hull3d_compute_async", "hull3d_compute",
     "hull3d_compute_host", "hull3d_batch_async", "hull3d_strerror", "hull3d_last_cuda_error",
-    "hull3d_last_launch_count", "hull3d_profile", "hull3d_profile_read", "hull3d_profile_levels", "hull3d_level_events",
+    "hull3d_last_launch_count", "hull3d_compute_static", "hull3d_profile", "hull3d_profile_read", "hull3d_profile_levels", "hull3d_level_events",
 )
 PHASES = ("sort", "fused", "levels", "seg", "faces")
 
@@ -80,6 +82,8 @@ def load():
             lib.hull3d_compute_host.restype = ctypes.c_int
             lib.hull3d_batch_async.argtypes = [P, P, P, i64, P, P, P, P, P]
             lib.hull3d_batch_async.restype = ctypes.c_int
+            lib.hull3d_compute_static.argtypes = [P, i64, P, i64, P, P, P]
+            lib.hull3d_compute_static.restype = ctypes.c_int
             lib.hull3d_strerror.argtypes = [ctypes.c_int]
             lib.hull3d_strerror.restype = ctypes.c_char_p
             lib.hull3d_last_cuda_error.argtypes = []

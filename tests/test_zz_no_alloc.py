@@ -1,0 +1,75 @@
+"""The allocation-free entry point, hull3d_compute_static.
+
+Some callers may not allocate device memory: code inside a host framework
+that owns the whole device through a fixed pool or budget, or latency-critical
+loops that cannot pay for cudaMalloc/cudaFree (which may synchronise the
+device).  hull3d_compute_static serves them: the caller passes input and
+output buffers, and the library's scratch comes from one static device array.
+
+This test calls it through the C ABI and checks that it gives exactly the
+faces of the planned entry point, on two calls in a row (the static array
+keeps the previous call's contents), and that sizes above its maximum are
+refused.  It is kept in its own file, collected last.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1205_1171_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1205_1171_gb300 import build, hull3d
+
+    build.build()
+    hull3d.load()
+    return hull3d
+
+
+def _static(H, x):
+    lib = H.load()
+    n = x.shape[0]
+    cap = max(2 * n - 4, 1)
+    faces = torch.full((cap, 3), -1, dtype=torch.int32, device="cuda")
+    nf = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = lib.hull3d_compute_static(x.data_ptr(), n, faces.data_ptr(), cap, nf.data_ptr(), st.data_ptr(), stream)
+    assert rc == 0, lib.hull3d_strerror(rc)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    return faces[: int(nf.item())].cpu().numpy()
+
+
+def test_static_entry_matches_planned_entry_on_consecutive_calls(H):
+    plan = H.Hull3D(H.STATIC_MAX_N)
+    try:
+        cases = [("sphere", 5000, 1), ("gauss", H.STATIC_MAX_N, 2), ("cube", 777, 3)]
+        for dist, n, seed in cases:
+            x = torch.from_numpy(inputs.cloud_seeded(dist, n, seed)).cuda()
+            want = plan.compute(x).cpu().numpy()
+            for _ in range(2):  # two calls in a row on the same shared array
+                got = _static(H, x)
+                assert got.shape == want.shape and np.array_equal(got, want), (dist, n)
+    finally:
+        plan.close()
+
+
+def test_static_entry_refuses_sizes_above_its_maximum(H):
+    lib = H.load()
+    n = H.STATIC_MAX_N + 1
+    x = torch.zeros((n, 3), dtype=torch.int32, device="cuda")
+    faces = torch.empty((2 * n, 3), dtype=torch.int32, device="cuda")
+    nf = torch.zeros(1, dtype=torch.int64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = lib.hull3d_compute_static(x.data_ptr(), n, faces.data_ptr(), 2 * n, nf.data_ptr(), st.data_ptr(),
+                                   torch.cuda.current_stream().cuda_stream)
+    assert rc == H.ERR_TOO_LARGE
+    assert b"HULL3D_STATIC_MAX_N" in lib.hull3d_strerror(rc)
