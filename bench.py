@@ -45,10 +45,10 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def make_inputs(rank: int, n: int = N_POINTS):
+def make_inputs(rank: int, n: int = N_POINTS, dists=DISTS):
     from paper_1205_1171_gb300 import inputs
 
-    return [inputs.cloud_seeded(d, n, inputs.seed_for(30 + i) + 1000 * rank) for i, d in enumerate(DISTS)]
+    return [inputs.cloud_seeded(d, n, inputs.seed_for(30 + i) + 1000 * rank) for i, d in enumerate(dists)]
 
 
 class ClockSampler:
@@ -172,6 +172,9 @@ def main():
     ap.add_argument("--occ", type=int, default=0, help="global merge kernel occupancy knob (1 or 4)")
     ap.add_argument("--cmp-level", type=int, default=0, help="first level of the compacted warp kernel (0 = default)")
     ap.add_argument("--n", type=int, default=1 << 24, help="points per cloud (profiling runs only; default 2^24)")
+    ap.add_argument("--dists", default=",".join(DISTS), help="clouds per step (profiling runs only)")
+    ap.add_argument("--seg-level", type=int, default=0, help="first time-segment-parallel level (0 = default)")
+    ap.add_argument("--seg-events", type=int, default=0, help="child events per time window (0 = default)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     npts = args.n
@@ -194,9 +197,11 @@ def main():
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
-    clouds = make_inputs(rank, npts)
+    dists = tuple(args.dists.split(","))
+    clouds = make_inputs(rank, npts, dists)
     dev_clouds = [torch.from_numpy(c).cuda() for c in clouds]
-    plan = hull3d.Hull3D(npts, fused_levels=args.fused, level_occupancy=args.occ, cmp_level=args.cmp_level)
+    plan = hull3d.Hull3D(npts, fused_levels=args.fused, level_occupancy=args.occ, cmp_level=args.cmp_level,
+                         seg_level=args.seg_level, seg_events=args.seg_events)
     cap = 2 * npts - 4
     faces = [torch.empty((cap, 3), dtype=torch.int32, device="cuda") for _ in clouds]
     nfs = [torch.zeros(1, dtype=torch.int64, device="cuda") for _ in clouds]

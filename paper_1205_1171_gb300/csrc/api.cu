@@ -103,6 +103,19 @@ struct hull3d_plan_s {
     size_t ev_used = 0;
     std::vector<int> marks;  // per recorded call: HULL3D_PHASES + 1 event indices
     std::vector<int> level_marks;  // per recorded level launch: (level, start event, end event)
+    // CUDA graphs of the whole pipeline, keyed by the call's arguments
+    struct GraphEntry {
+        const void *xyz;
+        int64_t n;
+        void *faces, *nf, *status;
+        cudaGraphExec_t exec;
+        int64_t launches;
+        uint64_t used;
+    };
+    static constexpr int kGraphs = 8;
+    GraphEntry graphs[kGraphs]{};
+    uint64_t graph_clock = 0;
+    cudaStream_t cap_stream = nullptr;  // private stream the pipeline is captured on
 };
 
 namespace {
@@ -214,7 +227,7 @@ int default_cmp_level(const hull3d_plan_s *p) { return p->opts.cmp_level > 0 ? p
 int default_cmp_slots(const hull3d_plan_s *p) { return p->opts.cmp_slots > 0 ? p->opts.cmp_slots : 1024; }
 int default_seg_level(const hull3d_plan_s *p) { return p->opts.seg_level > 0 ? p->opts.seg_level : 14; }
 int default_seg_events(const hull3d_plan_s *p) { return p->opts.seg_events > 0 ? p->opts.seg_events : 512; }
-int default_seg_slots(const hull3d_plan_s *p) { return p->opts.seg_slots > 0 ? p->opts.seg_slots : 2048; }
+int default_seg_slots(const hull3d_plan_s *p) { return p->opts.seg_slots > 0 ? p->opts.seg_slots : 1536; }
 
 // Records a phase-boundary event when profiling (one per boundary per call).
 int mark(hull3d_plan_s *p, cudaStream_t st, int *slot)
@@ -318,6 +331,43 @@ int enqueue_hull(hull3d_plan_s *p, const int32_t *d_xyz, int64_t n, int32_t *d_f
     return HULL3D_OK;
 }
 
+bool use_graphs(const hull3d_plan_s *p) { return p->opts.use_graph >= 0 && !p->profile && !debug_sync(); }
+
+// Enqueues the pipeline as a replay of a cached CUDA graph (captured on the
+// plan's private stream on first use of these arguments).
+int enqueue_hull_graph(hull3d_plan_s *p, const int32_t *d_xyz, int64_t n, int32_t *d_faces, int64_t *nf,
+                       int32_t *status, cudaStream_t st)
+{
+    hull3d_plan_s::GraphEntry *hit = nullptr, *victim = &p->graphs[0];
+    for (auto &g : p->graphs) {
+        if (g.exec && g.xyz == d_xyz && g.n == n && g.faces == d_faces && g.nf == nf && g.status == status) hit = &g;
+        if (!g.exec || g.used < victim->used) victim = &g;
+    }
+    if (!hit) {
+        if (!p->cap_stream) CK(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+        CK(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_hull(p, d_xyz, n, d_faces, nf, status, p->cap_stream);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(p->cap_stream, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e);
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e);
+        if (victim->exec) cudaGraphExecDestroy(victim->exec);
+        *victim = hull3d_plan_s::GraphEntry{ d_xyz, n, d_faces, nf, status, exec, p->last_launches, 0 };
+        hit = victim;
+    }
+    hit->used = ++p->graph_clock;
+    CK(cudaGraphLaunch(hit->exec, st));
+    p->last_launches = hit->launches;
+    return HULL3D_OK;
+}
+
 int check_compute_args(hull3d_plan_s *p, const void *xyz, int64_t n, const void *faces, int64_t cap)
 {
     if (!p || !xyz || n < 1 || n > p->max_n) return HULL3D_ERR_INVALID_ARG;
@@ -348,6 +398,8 @@ int hull3d_plan(hull3d_plan_t *out, int64_t max_n, int64_t max_clouds, const hul
         return HULL3D_ERR_INVALID_ARG;
     }
     cudaGetDevice(&p->device);
+    merge_kernel_attributes();
+    seg_kernel_attributes();
     p->pool_bytes = layout(p, nullptr);
     cudaError_t e = cudaMalloc((void **)&p->pool, p->pool_bytes);
     if (e != cudaSuccess) {
@@ -373,6 +425,9 @@ void hull3d_destroy(hull3d_plan_t p)
     if (!p) return;
     cudaDeviceSynchronize();
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    for (auto &g : p->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     cudaFree(p->pool);
     cudaFreeHost(p->h_nfaces);
     delete p;
@@ -401,8 +456,10 @@ int hull3d_compute_async(hull3d_plan_t p, const int32_t *d_xyz, int64_t n, int32
 {
     int rc = check_compute_args(p, d_xyz, n, d_faces, cap_faces);
     if (rc) return rc;
-    return enqueue_hull(p, d_xyz, n, d_faces, d_nfaces ? d_nfaces : p->nfaces, d_status ? d_status : p->status,
-                        (cudaStream_t)stream);
+    int64_t *nf = d_nfaces ? d_nfaces : p->nfaces;
+    int32_t *status = d_status ? d_status : p->status;
+    if (use_graphs(p)) return enqueue_hull_graph(p, d_xyz, n, d_faces, nf, status, (cudaStream_t)stream);
+    return enqueue_hull(p, d_xyz, n, d_faces, nf, status, (cudaStream_t)stream);
 }
 
 int hull3d_compute(hull3d_plan_t p, const int32_t *d_xyz, int64_t n, int32_t *d_faces, int64_t cap_faces,
@@ -411,7 +468,8 @@ int hull3d_compute(hull3d_plan_t p, const int32_t *d_xyz, int64_t n, int32_t *d_
     int rc = check_compute_args(p, d_xyz, n, d_faces, cap_faces);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    rc = enqueue_hull(p, d_xyz, n, d_faces, p->nfaces, p->status, st);
+    rc = use_graphs(p) ? enqueue_hull_graph(p, d_xyz, n, d_faces, p->nfaces, p->status, st)
+                       : enqueue_hull(p, d_xyz, n, d_faces, p->nfaces, p->status, st);
     if (rc) return rc;
     CK(cudaMemcpyAsync(p->h_nfaces, p->nfaces, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(p->h_status, p->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -427,7 +485,8 @@ int hull3d_compute_host(hull3d_plan_t p, const int32_t *h_xyz, int64_t n, int32_
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaMemcpyAsync(p->stage_xyz, h_xyz, (size_t)n * 3 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    rc = enqueue_hull(p, p->stage_xyz, n, p->stage_faces, p->nfaces, p->status, st);
+    rc = use_graphs(p) ? enqueue_hull_graph(p, p->stage_xyz, n, p->stage_faces, p->nfaces, p->status, st)
+                       : enqueue_hull(p, p->stage_xyz, n, p->stage_faces, p->nfaces, p->status, st);
     if (rc) return rc;
     CK(cudaMemcpyAsync(p->h_nfaces, p->nfaces, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(p->h_status, p->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));

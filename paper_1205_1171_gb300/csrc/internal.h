@@ -83,4 +83,8 @@ void launch_face_out(const uint64_t *keys, const uint32_t *vals, int64_t cap, in
 // Shared memory of the fused kernel for blocks of 2^l1 ranks.
 size_t fused_smem_bytes(int l1);
 
+// Kernel attributes (shared-memory limits), set once per process before any launch.
+void merge_kernel_attributes();
+void seg_kernel_attributes();
+
 }  // namespace hull3d

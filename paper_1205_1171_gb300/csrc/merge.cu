@@ -16,6 +16,8 @@ namespace hull3d {
 
 __device__ __forceinline__ void set_status2(int32_t *status, int code) { atomicCAS(status, 0, code); }
 
+size_t fused_smem_bytes(int l1);
+
 // ---------------------------------------------------------------------------
 // Level 1: pairs.  A pair's hull is its segment at every time: no events.
 // ---------------------------------------------------------------------------
@@ -217,19 +219,26 @@ __global__ void __launch_bounds__(CMP_THREADS) k_level_cmp(Points pts, int64_t n
         }
     }
     __syncthreads();
-    if (tid == 0) {
-        int k = 0;
-        if (!s_bad) {
-            CPts cp{ sPt, sRK };
-            CLinks lk{ sLk };
-            CEvIn L{ sIn }, R{ sIn + nl };
-            CEvOut out{ sOut, Wdst + 2 * lo, Adst + 2 * lo, Bdst + 2 * lo, sRK };
-            int err = 0;
-            k = kinetic_merge(cp, lk, gmap[e1], gmap[e2], (int)mid, L, nl, R, nr, out, min(cap, 2 * scap), upper,
-                              &err);
+    if (!s_bad) {
+        CPts cp{ sPt, sRK };
+        CLinks lk{ sLk };
+        CEvIn L{ sIn }, R{ sIn + nl };
+        CEvOut out{ sOut, Wdst + 2 * lo, Adst + 2 * lo, Bdst + 2 * lo, sRK };
+        int err = 0;
+        int u = gmap[e1], v = gmap[e2];
+        if (tid == 0) bridge_walk(cp, lk, u, v, (const Tri *)nullptr, upper);  // follows links: serial
+        u = __shfl_sync(0xffffffffu, u, 0);
+        v = __shfl_sync(0xffffffffu, v, 0);
+        Tri none;
+        none.p = none.q = none.r = -2;
+        none.s = 0;
+        const int k = kinetic_forward_warp(cp, lk, u, v, none, false, L, nl, R, nr, out, min(cap, 2 * scap), upper,
+                                           false, &err);
+        if (tid == 0) {
             if (err) s_bad = 1;
+            else kinetic_backward(cp, lk, u, v, (int)mid, out, k);
+            s_k = k;
         }
-        s_k = k;
     }
     __syncthreads();
     if (s_bad) {
@@ -251,14 +260,10 @@ __global__ void __launch_bounds__(CMP_THREADS) k_level_cmp(Points pts, int64_t n
 
 size_t cmp_smem_bytes(int scap) { return (size_t)scap * (sizeof(int4) + sizeof(int2) + 4 * sizeof(int)); }
 
+
 void launch_level_cmp(const Points &pts, int64_t n, int level, PassBufs *passes, int npass, int32_t *status,
                       cudaStream_t st, int scap)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_level_cmp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cmp_smem_bytes(4096));
-        attr_set = true;
-    }
     int64_t nodes = (n + (1ll << level) - 1) >> level;
     dim3 g((unsigned)nodes, npass);
     k_level_cmp<<<g, CMP_THREADS, cmp_smem_bytes(scap), st>>>(pts, n, level, passes[0], passes[npass - 1], scap,
@@ -368,12 +373,6 @@ void launch_fused(const Points &pts, int64_t n, int l0, int l1, PassBufs *passes
     (void)l0;
     int64_t blocks = (n + (1ll << l1) - 1) >> l1;
     size_t smem = fused_smem_bytes(l1);
-    // the attribute is per kernel: raise it once to the largest depth's need
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem_bytes(10));
-        attr_set = true;
-    }
     // one thread per bottom merge: 2^(l1-1) threads, at least a warp
     int threads = 1 << (l1 - 1);
     if (threads < 32) threads = 32;
@@ -442,6 +441,14 @@ void launch_face_out(const uint64_t *keys, const uint32_t *vals, int64_t cap, in
                           int32_t *faces, cudaStream_t st)
 {
     k_face_out<<<(unsigned)((cap + 255) / 256), 256, 0, st>>>(keys, vals, fbits, d_nfaces, faces);
+}
+
+// Shared-memory limits of the kernels that need more than the default; set
+// once, before any launch or stream capture.
+void merge_kernel_attributes()
+{
+    cudaFuncSetAttribute(k_level_cmp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cmp_smem_bytes(4096));
+    cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem_bytes(10));
 }
 
 }  // namespace hull3d

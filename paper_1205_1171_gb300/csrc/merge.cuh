@@ -55,24 +55,25 @@ __device__ __forceinline__ void tri_make(const PT &pt, Tri &t, int p, int q, int
     else t.s = turn_slow(P, Q, R);
 }
 
+// The tie tiers of tri_cmp (unperturbed times equal), out of line.
+template <class PT>
+__device__ __noinline__ int tri_cmp_tie(const PT &pt, const Tri &a, const Tri &b)
+{
+    if (a.p == b.p && a.q == b.q && a.r == b.r) return 0;
+    // shear tiers: -c.z then -c.y with c = N1 x N2, N = (Nx, -Z, Y)
+    i128 cz = (i128)a.Z * b.Nx - (i128)a.Nx * b.Z;
+    if (cz != 0) return -sgn128(cz) * a.s * b.s;
+    i128 cy = (i128)a.Y * b.Nx - (i128)a.Nx * b.Y;
+    if (cy != 0) return -sgn128(cy) * a.s * b.s;
+    return time_cmp_index(pt, a.p, a.q, a.r, b.p, b.q, b.r, a.s * b.s);
+}
+
 // sign(t(a) - t(b)) in the pass's time direction, both finite.
 template <class PT>
-__device__ __noinline__ int tri_cmp(const PT &pt, const Tri &a, const Tri &b, bool upper)
+__device__ __forceinline__ int tri_cmp(const PT &pt, const Tri &a, const Tri &b, bool upper)
 {
     i128 D0 = (i128)a.Z * b.Y - (i128)b.Z * a.Y;
-    int s;
-    if (D0 != 0) {
-        s = sgn128(D0) * a.s * b.s;
-    } else if (a.p == b.p && a.q == b.q && a.r == b.r) {
-        s = 0;
-    } else {
-        // shear tiers: -c.z then -c.y with c = N1 x N2, N = (Nx, -Z, Y)
-        i128 cz = (i128)a.Z * b.Nx - (i128)a.Nx * b.Z;
-        i128 cy = (i128)a.Y * b.Nx - (i128)a.Nx * b.Y;
-        if (cz != 0) s = -sgn128(cz) * a.s * b.s;
-        else if (cy != 0) s = -sgn128(cy) * a.s * b.s;
-        else s = time_cmp_index(pt, a.p, a.q, a.r, b.p, b.q, b.r, a.s * b.s);
-    }
+    int s = D0 != 0 ? sgn128(D0) * a.s * b.s : tri_cmp_tie(pt, a, b);
     return upper ? -s : s;
 }
 
@@ -196,6 +197,122 @@ __device__ int kinetic_forward(const PT &pt, LK &lk, int &u, int &v, Tri old, bo
     }
     return k;
 }
+
+#ifdef __CUDACC__
+__device__ __forceinline__ Tri shfl_tri(const Tri &t, int src, unsigned mask = 0xffffffffu)
+{
+    Tri r;
+    r.p = __shfl_sync(mask, t.p, src);
+    r.q = __shfl_sync(mask, t.q, src);
+    r.r = __shfl_sync(mask, t.r, src);
+    r.s = __shfl_sync(mask, t.s, src);
+    r.Z = __shfl_sync(mask, t.Z, src);
+    r.Y = __shfl_sync(mask, t.Y, src);
+    r.Nx = __shfl_sync(mask, t.Nx, src);
+    return r;
+}
+
+// Warp-cooperative forward pass: the same loop as kinetic_forward, entered
+// by all 32 lanes with identical arguments.  Lane l < 6 owns candidate l and
+// refreshes it in parallel with the others; a three-step shuffle reduction
+// finds the earliest valid candidate; lane 0 applies the event to the shared
+// links and the output while every lane advances the (identical) loop state.
+template <class PT, class LK, class EIN, class EOUT>
+__device__ int kinetic_forward_warp(const PT &pt, LK &lk, int &u, int &v, Tri old, bool have_old, const EIN &L,
+                                    int nl, const EIN &R, int nr, EOUT &out, int cap, bool upper, bool stop_at_end,
+                                    int *err)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    Tri c;
+    c.p = c.q = c.r = -2;
+    c.s = 0;
+    bool valid = false;
+    int i = 0, j = 0, k = 0;
+    for (;;) {
+        if (stop_at_end && i >= nl && j >= nr) break;
+        if (lane < 6) {
+            int tp = NIL, tq = NIL, tr = NIL;
+            if (lane == 0) {
+                if (i < nl) { tq = (int)(L.w(i) & RANK_MASK); int2 l0 = lk.get(tq); tp = l0.x; tr = l0.y; }
+            } else if (lane == 1) {
+                if (j < nr) { tq = (int)(R.w(j) & RANK_MASK); int2 l1 = lk.get(tq); tp = l1.x; tr = l1.y; }
+            } else if (lane == 2) { tp = u; tq = lk.nxt(u); tr = v; }
+            else if (lane == 3) { tp = lk.prv(u); tq = u; tr = v; }
+            else if (lane == 4) { tp = u; tq = lk.prv(v); tr = v; }
+            else { tp = u; tq = v; tr = lk.nxt(v); }
+            if (tp != c.p || tq != c.q || tr != c.r) {
+                tri_make(pt, c, tp, tq, tr);
+                valid = c.s != 0 && (!have_old || tri_cmp(pt, c, old, upper) > 0);
+            }
+        }
+        int bi = (lane < 6 && valid) ? lane : -1;
+        Tri bt = c;
+#pragma unroll
+        for (int off = 4; off >= 1; off >>= 1) {
+            const int oi = __shfl_down_sync(FULL, bi, off);
+            const Tri ot = shfl_tri(bt, (lane + off) & 31);
+            if (lane < 8 && oi >= 0 && (bi < 0 || tri_cmp(pt, ot, bt, upper) < 0)) { bi = oi; bt = ot; }
+        }
+        const int best = __shfl_sync(FULL, bi, 0);
+        if (best < 0) break;
+        const Tri t = shfl_tri(bt, 0);
+        if (k >= cap) { *err = 1; return cap; }
+        if (best <= 1) {
+            const int e = t.q;
+            const bool vis = best == 0 ? pt.rk(e) < pt.rk(u) : pt.rk(e) > pt.rk(v);
+            if (best == 0) i++; else j++;
+            if (lane == 0) {
+                if (vis) out.put(k, (unsigned)e | (lk.nxt(t.p) != e ? INS_BIT : 0u), t.p, t.r);
+                act(lk, e);
+            }
+            k += vis ? 1 : 0;
+        } else {
+            const bool ins = (best == 2) | (best == 4);
+            if (lane == 0) out.put(k, (unsigned)t.q | (ins ? INS_BIT : 0u), t.p, t.r);
+            k++;
+            if (best == 2) u = t.q;
+            else if (best == 3) u = t.p;
+            else if (best == 4) v = t.q;
+            else v = t.r;
+        }
+        __syncwarp();
+        old = t;
+        have_old = true;
+        if (lane == best) valid = false;
+    }
+    return k;
+}
+
+// Warp-parallel version of bridge_walk for two chains stored as consecutive
+// slots (left chain ends at slot u, right chain starts at slot v, lengths
+// given by u_first and v_last): each step tests 32 consecutive chain links at
+// once and jumps to the first one that stops the serial walk, so it ends at
+// the serial walk's bridge.
+template <class PT>
+__device__ void bridge_walk_warp(const PT &pt, int u_first, int v_last, int &u, int &v, const Tri *at, bool upper)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        // advance v while (u, v, v.next) turns right, 32 links per step
+        for (;;) {
+            const int a = v + lane;
+            const bool right = a + 1 <= v_last && turn_after(pt, u, a, a + 1, at, upper) < 0;
+            const unsigned bal = __ballot_sync(FULL, right);
+            const int run = bal == FULL ? 32 : __ffs(~bal) - 1;  // consecutive right turns from v
+            v += run;
+            if (run < 32) break;
+        }
+        // then move u back one step if (u.prev, u, v) turns right, and retry v
+        if (u > u_first && turn_after(pt, u - 1, u, v, at, upper) < 0) {
+            u -= 1;
+            continue;
+        }
+        break;
+    }
+}
+#endif
 
 // Backward pass (step 3): from the t = +infinity bridge (u, v) undo the
 // parent's k events in reverse, leaving the parent's t = -infinity hull and

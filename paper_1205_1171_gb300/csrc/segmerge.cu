@@ -164,6 +164,7 @@ struct SegIn {
 };
 
 constexpr int SEG_THREADS = 32;
+constexpr int SEG_SLOTS_BIG = 6144;  // retry table (about 170 KB of shared memory)
 
 // first index in [0, cnt) of keys >= key
 __device__ __forceinline__ int64_t lower_key(const uint64_t *keys, int64_t cnt, uint64_t key)
@@ -176,7 +177,11 @@ __device__ __forceinline__ int64_t lower_key(const uint64_t *keys, int64_t cnt, 
     return lo;
 }
 
-__global__ void __launch_bounds__(SEG_THREADS) k_seg_merge(SegArgs a)
+// retry = 0: every window, slot table of geo.scap; a window that does not fit
+// marks itself with ocnt = -1.  retry = 1: only those windows, with a table of
+// scap_big; a window that still does not fit sends its merge to the serial
+// fallback.
+__global__ void __launch_bounds__(SEG_THREADS) k_seg_merge(SegArgs a, int retry, int scap_big)
 {
     extern __shared__ int sm[];
     __shared__ int s_bad, s_nins;
@@ -197,6 +202,8 @@ __global__ void __launch_bounds__(SEG_THREADS) k_seg_merge(SegArgs a)
     const int S = sb.nseg[m];
     if (s >= S) return;
     if (*a.overflow) { if (threadIdx.x == 0) sb.nofit[m] = 1; return; }
+    if (retry && sb.ocnt[g] != -1) return;
+    const int scap = retry ? scap_big : G.scap;
     const int tid = threadIdx.x;
     const int src = (G.level - 1) & 1;
     const int nl = pb.cnt[src][lo], nr = pb.cnt[src][mid];
@@ -223,14 +230,21 @@ __global__ void __launch_bounds__(SEG_THREADS) k_seg_merge(SegArgs a)
     const int nins = s_nins;
     const int base_ins = aL + aR;
     const int tsize = base_ins + nins + 3;  // + the three points of the window's boundary event
-    if (tsize > G.scap || wl + wr > G.K + 1 || aL < 1 || aR < 1) {
+    if (wl + wr > G.K + 1 || aL < 1 || aR < 1) {  // cannot happen for valid movies
         if (tid == 0) sb.nofit[m] = 1;
         return;
     }
+    if (tsize > scap) {
+        if (tid == 0) {
+            if (retry) sb.nofit[m] = 1;
+            else sb.ocnt[g] = -1;
+        }
+        return;
+    }
     int4 *sPt = (int4 *)sm;
-    int2 *sLk = (int2 *)(sPt + G.scap);
-    int *sRK = (int *)(sLk + G.scap);
-    unsigned *sIn = (unsigned *)(sRK + G.scap);  // window movies as slots: left then right
+    int2 *sLk = (int2 *)(sPt + scap);
+    int *sRK = (int *)(sLk + scap);
+    unsigned *sIn = (unsigned *)(sRK + scap);  // window movies as slots: left then right
     // start hulls, linked in x-order
     for (int i = tid; i < aL + aR; i += SEG_THREADS) {
         const bool left = i < aL;
@@ -287,41 +301,46 @@ __global__ void __launch_bounds__(SEG_THREADS) k_seg_merge(SegArgs a)
         sIn[e] = (unsigned)find((int)(w & RANK_MASK), left ? 0 : 1) | (w & INS_BIT);
     }
     __syncthreads();
-    if (tid == 0 && !s_bad) {
+    if (!s_bad) {
         CPts cp{ sPt, sRK };
         CLinks lk{ sLk };
         Tri at;
         at.s = 0;
+        const int tb = base_ins + nins;
         if (s > 0) {  // the window starts just after the latest child event before it
-            GPts gp{ a.pts.P };
-            const int *A = pb.A[src], *B = pb.B[src];
-            int eb = -1;  // global index of that event in the source buffer
-            if (b0.x > 0 && b0.y > 0) {
-                Tri tl, tr;
-                ev_tri(gp, pb.W[src], A, B, (int)(2 * lo) + b0.x - 1, tl);
-                ev_tri(gp, pb.W[src], A, B, (int)(2 * mid) + b0.y - 1, tr);
-                eb = tri_cmp(gp, tl, tr, upper) > 0 ? (int)(2 * lo) + b0.x - 1 : (int)(2 * mid) + b0.y - 1;
-            } else {
-                eb = b0.x > 0 ? (int)(2 * lo) + b0.x - 1 : (int)(2 * mid) + b0.y - 1;
+            if (tid == 0) {
+                GPts gp{ a.pts.P };
+                const int *A = pb.A[src], *B = pb.B[src];
+                int eb;  // index of that event in the source buffer
+                if (b0.x > 0 && b0.y > 0) {
+                    Tri tl, tr;
+                    ev_tri(gp, pb.W[src], A, B, (int)(2 * lo) + b0.x - 1, tl);
+                    ev_tri(gp, pb.W[src], A, B, (int)(2 * mid) + b0.y - 1, tr);
+                    eb = tri_cmp(gp, tl, tr, upper) > 0 ? (int)(2 * lo) + b0.x - 1 : (int)(2 * mid) + b0.y - 1;
+                } else {
+                    eb = b0.x > 0 ? (int)(2 * lo) + b0.x - 1 : (int)(2 * mid) + b0.y - 1;
+                }
+                const int rr[3] = { A[eb], (int)(pb.W[src][eb] & RANK_MASK), B[eb] };
+                for (int q = 0; q < 3; q++) {
+                    sRK[tb + q] = rr[q];
+                    sPt[tb + q] = a.pts.P[rr[q]];
+                    sLk[tb + q] = make_int2(NIL, NIL);
+                }
             }
-            const int tb = base_ins + nins;
-            const int rr[3] = { A[eb], (int)(pb.W[src][eb] & RANK_MASK), B[eb] };
-            for (int q = 0; q < 3; q++) {
-                sRK[tb + q] = rr[q];
-                sPt[tb + q] = a.pts.P[rr[q]];
-                sLk[tb + q] = make_int2(NIL, NIL);
-            }
+            __syncwarp();
             tri_make(cp, at, tb, tb + 1, tb + 2);
         }
         int u = aL - 1, v = aL;  // the inner x-extremes mid - 1 and mid
-        bridge_walk(cp, lk, u, v, s > 0 ? &at : (const Tri *)nullptr, upper);
-        if (s == 0) sb.bridge0[m] = make_int2(sRK[u], sRK[v]);
+        bridge_walk_warp(cp, 0, aL + aR - 1, u, v, s > 0 ? &at : (const Tri *)nullptr, upper);
+        if (s == 0 && tid == 0) sb.bridge0[m] = make_int2(sRK[u], sRK[v]);
         SegIn L{ sIn }, R{ sIn + wl };
         SegOut out{ sb.oW + g * G.ocap, sb.oA + g * G.ocap, sb.oB + g * G.ocap, sRK };
         int err = 0;
-        int k = kinetic_forward(cp, lk, u, v, at, s > 0, L, wl, R, wr, out, G.ocap, upper, s + 1 < S, &err);
-        sb.ocnt[g] = k;
-        if (err) s_bad = 1;
+        const int k = kinetic_forward_warp(cp, lk, u, v, at, s > 0, L, wl, R, wr, out, G.ocap, upper, s + 1 < S, &err);
+        if (tid == 0) {
+            sb.ocnt[g] = k;
+            if (err) s_bad = 1;
+        }
     }
     __syncthreads();
     if (tid == 0 && s_bad) sb.nofit[m] = 1;
@@ -413,6 +432,11 @@ __global__ void k_seg_fallback(SegArgs a)
     atomicAdd(pb.lev_events + G.level, (unsigned long long)k);
 }
 
+void seg_kernel_attributes()
+{
+    cudaFuncSetAttribute(k_seg_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
 size_t seg_smem_bytes(int scap, int K) { return (size_t)scap * (sizeof(int4) + sizeof(int2) + sizeof(int)) + 4 * (K + 1); }
 
 void launch_seg_level(const Points &pts, int64_t n, int level, PassBufs *passes, SegBufs *sbufs, uint64_t *pairs,
@@ -454,15 +478,11 @@ void launch_seg_level(const Points &pts, int64_t n, int level, PassBufs *passes,
                                  st, launches);
     a.pairs = which ? pairs_alt : pairs;
     a.pair_vals = which ? vals_alt : pair_vals;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_seg_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
-    k_seg_merge<<<dim3((unsigned)G, 2), SEG_THREADS, seg_smem_bytes(scap, K), st>>>(a);
+    k_seg_merge<<<dim3((unsigned)G, 2), SEG_THREADS, seg_smem_bytes(scap, K), st>>>(a, 0, scap);
+    k_seg_merge<<<dim3((unsigned)G, 2), SEG_THREADS, seg_smem_bytes(SEG_SLOTS_BIG, K), st>>>(a, 1, SEG_SLOTS_BIG);
     k_seg_concat<<<dim3((unsigned)M, 2), CAT_THREADS, 0, st>>>(a);
     k_seg_fallback<<<dim3((unsigned)((M + 31) / 32), 2), 32, 0, st>>>(a);
-    *launches += 3;
+    *launches += 4;
     const int64_t last_lo = (M - 1) << level;
     if (last_lo + (1ll << (level - 1)) >= n) {
         launch_passthrough(n, level, last_lo, passes, status, st);

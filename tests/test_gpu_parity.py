@@ -201,3 +201,23 @@ def test_2e20_bit_exact(H, dist):
     p.close()
     want = oracle.hull(pts)
     assert np.array_equal(got, want)
+
+
+def test_graph_replay_matches_plain_launches(H):
+    """The level driver replayed as cached CUDA graphs (more argument sets than
+    cache entries, so entries are evicted and recaptured) gives the same faces
+    as plain launches."""
+    g = H.Hull3D(1 << 15)
+    plain = H.Hull3D(1 << 15, use_graph=-1)
+    try:
+        clouds = [torch.from_numpy(inputs.cloud_seeded(d, n, 60 + n)).cuda()
+                  for d in inputs.DISTS for n in (300, 9000, 1 << 15)]
+        for rep in range(3):
+            for x in clouds:
+                got = g.compute(x).cpu().numpy()
+                want = plain.compute(x).cpu().numpy()
+                assert np.array_equal(got, want)
+        assert g.last_launches > 0
+    finally:
+        g.close()
+        plain.close()
