@@ -5,6 +5,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+#include <climits>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -116,6 +118,12 @@ struct hull3d_plan_s {
     GraphEntry graphs[kGraphs]{};
     uint64_t graph_clock = 0;
     cudaStream_t cap_stream = nullptr;  // private stream the pipeline is captured on
+    // batched clouds: per-cloud metadata uploaded for the persistent kernels
+    int64_t *b_off = nullptr, *b_foff = nullptr;
+    int32_t *b_order = nullptr;
+    int *b_counter = nullptr;
+    std::vector<int32_t> h_order;
+    int sms = 0;
 };
 
 namespace {
@@ -205,6 +213,10 @@ size_t layout(hull3d_plan_s *p, char *base)
         }
     }
     p->lev_stats = b.take<unsigned long long>(128);
+    p->b_off = b.take<int64_t>(p->max_clouds + 1);
+    p->b_foff = b.take<int64_t>(p->max_clouds + 1);
+    p->b_order = b.take<int32_t>(p->max_clouds + 1);
+    p->b_counter = b.take<int>(BATCH_CLASSES);
     p->pass[0].lev_events = p->lev_stats;
     p->pass[1].lev_events = p->lev_stats + 64;
     p->status = b.take<int32_t>(1);
@@ -225,7 +237,11 @@ int default_occupancy(const hull3d_plan_s *p, int level)
 }
 int default_cmp_level(const hull3d_plan_s *p) { return p->opts.cmp_level > 0 ? p->opts.cmp_level : 13; }
 int default_cmp_slots(const hull3d_plan_s *p) { return p->opts.cmp_slots > 0 ? p->opts.cmp_slots : 1024; }
-int default_seg_level(const hull3d_plan_s *p) { return p->opts.seg_level > 0 ? p->opts.seg_level : 14; }
+int default_seg_level(const hull3d_plan_s *p) { return p->opts.seg_level > 0 ? p->opts.seg_level : 10; }
+int default_seg_min_events(const hull3d_plan_s *p)
+{
+    return p->opts.seg_min_events > 0 ? p->opts.seg_min_events : 4096;
+}
 int default_seg_events(const hull3d_plan_s *p) { return p->opts.seg_events > 0 ? p->opts.seg_events : 512; }
 int default_seg_slots(const hull3d_plan_s *p) { return p->opts.seg_slots > 0 ? p->opts.seg_slots : 1536; }
 
@@ -293,9 +309,13 @@ int enqueue_hull(hull3d_plan_s *p, const int32_t *d_xyz, int64_t n, int32_t *d_f
         int lv0 = -1, lv1 = -1;
         if (p->profile) { int r_ = mark(p, st, &lv0); if (r_) return r_; }
         if (seg) {
+            // small merges on the compacted warp kernel, large ones in time windows
+            const int min_ev = default_seg_min_events(p);
+            launch_level_cmp(pts, n, level, p->pass, 2, status, st, default_cmp_slots(p), min_ev);
+            launches++;
             launch_seg_level(pts, n, level, p->pass, p->seg, p->pk0, p->pv0, p->pk1, p->pv1, p->npairs, p->overflow,
-                             p->pair_cap, p->S_cap, p->M_cap, default_seg_events(p), default_seg_slots(p), p->ss, status,
-                             st, &launches);
+                             p->pair_cap, p->S_cap, p->M_cap, default_seg_events(p), default_seg_slots(p), min_ev, p->ss,
+                             status, st, &launches);
         } else {
             if (level >= default_cmp_level(p))
                 launch_level_cmp(pts, n, level, p->pass, 2, status, st, default_cmp_slots(p));
@@ -400,6 +420,8 @@ int hull3d_plan(hull3d_plan_t *out, int64_t max_n, int64_t max_clouds, const hul
     cudaGetDevice(&p->device);
     merge_kernel_attributes();
     seg_kernel_attributes();
+    batch_kernel_attributes();
+    cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
     p->pool_bytes = layout(p, nullptr);
     cudaError_t e = cudaMalloc((void **)&p->pool, p->pool_bytes);
     if (e != cudaSuccess) {
@@ -446,6 +468,7 @@ int hull3d_plan_opts(hull3d_plan_t p, hull3d_opts *out)
     out->seg_level = default_seg_level(p);
     out->seg_events = default_seg_events(p);
     out->seg_slots = default_seg_slots(p);
+    out->seg_min_events = default_seg_min_events(p);
     return HULL3D_OK;
 }
 
@@ -506,23 +529,66 @@ int hull3d_batch_async(hull3d_plan_t p, const int32_t *d_xyz, const int64_t *h_o
 {
     if (!p || !h_offsets || !h_face_offsets || B < 0 || (B > 0 && (!d_xyz || !d_faces || !d_nfaces || !d_status)))
         return HULL3D_ERR_INVALID_ARG;
+    if (B > p->max_clouds) return HULL3D_ERR_INVALID_ARG;
     if (h_offsets[0] != 0 || h_face_offsets[0] != 0) return HULL3D_ERR_INVALID_ARG;
+    const int small_max = batch_class_limit(BATCH_CLASSES - 1);
     for (int64_t b = 0; b < B; b++) {
         int64_t nb = h_offsets[b + 1] - h_offsets[b];
         int64_t cap = h_face_offsets[b + 1] - h_face_offsets[b];
-        if (nb < 1 || nb > p->max_n || cap < 0) return HULL3D_ERR_INVALID_ARG;
+        if (nb < 1 || cap < 0) return HULL3D_ERR_INVALID_ARG;
+        if (nb > small_max && nb > p->max_n) return HULL3D_ERR_INVALID_ARG;
         if (nb >= 3 && cap < 2 * nb - 4) return HULL3D_ERR_CAPACITY;
     }
+    if (B == 0) return HULL3D_OK;
     cudaStream_t st = (cudaStream_t)stream;
+    // size classes, largest clouds first inside each class
+    std::vector<int32_t> &ord = p->h_order;
+    ord.resize((size_t)B);
+    int64_t cls_begin[BATCH_CLASSES + 1] = {};
+    {
+        std::vector<int32_t> idx((size_t)B);
+        for (int64_t b = 0; b < B; b++) idx[b] = (int32_t)b;
+        auto size = [&](int32_t b) { return h_offsets[b + 1] - h_offsets[b]; };
+        std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t c) { return size(a) > size(c); });
+        // idx is by decreasing size: big clouds, then class 2, 1, 0
+        int64_t pos = 0;
+        for (int c = BATCH_CLASSES; c >= 0; c--) {
+            const int64_t lo_lim = c == 0 ? 0 : batch_class_limit(c - 1);
+            const int64_t hi_lim = c == BATCH_CLASSES ? INT64_MAX : batch_class_limit(c);
+            cls_begin[c] = pos;
+            for (int32_t b : idx) {
+                int64_t nb = size(b);
+                if (nb > lo_lim && nb <= hi_lim) ord[pos++] = b;
+            }
+        }
+    }
+    CK(cudaMemcpyAsync(p->b_off, h_offsets, sizeof(int64_t) * (size_t)(B + 1), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(p->b_foff, h_face_offsets, sizeof(int64_t) * (size_t)(B + 1), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(p->b_order, ord.data(), sizeof(int32_t) * (size_t)B, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(p->b_counter, 0, sizeof(int) * BATCH_CLASSES, st));
     int64_t launches = 0;
-    for (int64_t b = 0; b < B; b++) {
-        int64_t nb = h_offsets[b + 1] - h_offsets[b];
+    for (int c = 0; c < BATCH_CLASSES; c++) {
+        // classes were laid out big, 2, 1, 0: class c starts at cls_begin[c]
+        const int64_t begin = cls_begin[c];
+        const int64_t end = c == 0 ? B : cls_begin[c - 1];
+        const int count = (int)(end - begin);
+        if (count <= 0) continue;
+        launch_batch_class(c, d_xyz, p->b_off, p->b_foff, p->b_order + begin, count, p->b_counter + c, d_faces,
+                           d_nfaces, d_status, p->sms, st);
+        launches++;
+    }
+    // clouds above the largest class: the plain pipeline, one after the other
+    for (int64_t q = cls_begin[BATCH_CLASSES]; q < cls_begin[BATCH_CLASSES - 1]; q++) {
+        const int32_t b = ord[q];
+        const int64_t nb = h_offsets[b + 1] - h_offsets[b];
         int rc = enqueue_hull(p, d_xyz + 3 * h_offsets[b], nb, d_faces + 3 * h_face_offsets[b], d_nfaces + b,
                               d_status + b, st);
         if (rc) return rc;
         launches += p->last_launches;
     }
     p->last_launches = launches;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e);
     return HULL3D_OK;
 }
 

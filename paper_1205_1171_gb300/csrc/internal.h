@@ -56,8 +56,11 @@ void launch_level(const Points &pts, int64_t n, int level, PassBufs *passes, int
 
 // One level (>= 2), one warp per merge on a compacted shared-memory table of
 // up to scap slots (merges that do not fit run the global-memory merge).
+// With max_events >= 0 only merges of at most max_events child events are
+// done (the others are left to the time-segment kernels, which also copy the
+// pass-through node).
 void launch_level_cmp(const Points &pts, int64_t n, int level, PassBufs *passes, int npass, int32_t *status,
-                      cudaStream_t st, int scap);
+                      cudaStream_t st, int scap, int max_events = -1);
 
 // Copies the movie of the last node of a level when it has no right child.
 void launch_passthrough(int64_t n, int level, int64_t lo, PassBufs *passes, int32_t *status, cudaStream_t st);
@@ -69,7 +72,7 @@ struct SegBufs;
 void launch_seg_level(const Points &pts, int64_t n, int level, PassBufs *passes, SegBufs *sbufs, uint64_t *pairs,
                       uint32_t *pair_vals, uint64_t *pairs_alt, uint32_t *vals_alt, unsigned long long *npairs,
                       int *overflow, int64_t pair_cap, int64_t S_cap, int64_t M_cap, int K, int scap,
-                      const SortScratch &ss, int32_t *status, cudaStream_t st, int64_t *launches);
+                      int min_events, const SortScratch &ss, int32_t *status, cudaStream_t st, int64_t *launches);
 
 // Faces of the root movies of both passes (level L = ceil(log2 n) in buffer L & 1):
 // orient, rotate min-first, build the sort key (f0 << 28 | f1) and value f2.
@@ -86,5 +89,15 @@ size_t fused_smem_bytes(int l1);
 // Kernel attributes (shared-memory limits), set once per process before any launch.
 void merge_kernel_attributes();
 void seg_kernel_attributes();
+void batch_kernel_attributes();
+
+// Batched clouds: size class c (0, 1, 2) holds clouds of at most
+// batch_class_limit(c) points; one persistent launch hulls `count` clouds
+// listed in order[] (cloud indices into off/foff), pulling work from *counter.
+constexpr int BATCH_CLASSES = 3;
+int batch_class_limit(int c);
+void launch_batch_class(int c, const int32_t *xyz, const int64_t *off, const int64_t *foff, const int32_t *order,
+                        int count, int *counter, int32_t *faces, int64_t *nfaces, int32_t *status, int sms,
+                        cudaStream_t st);
 
 }  // namespace hull3d

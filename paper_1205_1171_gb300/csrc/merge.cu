@@ -144,8 +144,10 @@ struct CEvOut {  // slots stay in shared memory (backward pass), ranks go to glo
 
 constexpr int CMP_THREADS = 32;
 
+// Merges with more than max_events child events are left to the time-segment
+// kernels (max_events < 0: none).
 __global__ void __launch_bounds__(CMP_THREADS) k_level_cmp(Points pts, int64_t n, int level, PassBufs p0, PassBufs p1,
-                                                           int scap, int32_t *status)
+                                                           int scap, int max_events, int32_t *status)
 {
     extern __shared__ int sm[];
     __shared__ int s_k, s_bad;
@@ -165,6 +167,7 @@ __global__ void __launch_bounds__(CMP_THREADS) k_level_cmp(Points pts, int64_t n
     int2 *glk = upper ? p1.lk : p0.lk;
     int *gmap = upper ? p1.gmap : p0.gmap;
     const int nl = csrc[lo], nr = csrc[mid];
+    if (max_events >= 0 && nl + nr > max_events) return;
     const int ns = nl + nr + 4;
     const int tid = threadIdx.x;
     const int cap = (int)(2 * (hi - lo));
@@ -262,14 +265,14 @@ size_t cmp_smem_bytes(int scap) { return (size_t)scap * (sizeof(int4) + sizeof(i
 
 
 void launch_level_cmp(const Points &pts, int64_t n, int level, PassBufs *passes, int npass, int32_t *status,
-                      cudaStream_t st, int scap)
+                      cudaStream_t st, int scap, int max_events)
 {
     int64_t nodes = (n + (1ll << level) - 1) >> level;
     dim3 g((unsigned)nodes, npass);
     k_level_cmp<<<g, CMP_THREADS, cmp_smem_bytes(scap), st>>>(pts, n, level, passes[0], passes[npass - 1], scap,
-                                                              status);
+                                                              max_events, status);
     int64_t lo = (nodes - 1) << level;
-    if (lo + (1ll << (level - 1)) >= n) launch_passthrough(n, level, lo, passes, status, st);
+    if (max_events < 0 && lo + (1ll << (level - 1)) >= n) launch_passthrough(n, level, lo, passes, status, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -37,7 +37,8 @@ __global__ void k_seg_bounds(SegArgs a)
     const SegBufs &sb = a.sb[pass];
     const int src = (G.level - 1) & 1;
     const int nl = pb.cnt[src][lo], nr = pb.cnt[src][mid];
-    const int S = seg_count(nl, nr, G.K, G.smax);
+    // small merges are done by the compacted kernel: no windows
+    const int S = (nl + nr > G.min_events) ? seg_count(nl, nr, G.K, G.smax) : 0;
     if (s == 0) { sb.nseg[m] = S; sb.nofit[m] = 0; }
     if (s >= S) return;
     const int64_t g = m * G.smax + s;
@@ -366,6 +367,7 @@ __global__ void __launch_bounds__(CAT_THREADS) k_seg_concat(SegArgs a)
     if (sb.nofit[m]) return;  // merged serially by k_seg_fallback
     const int dst = G.level & 1;
     const int S = sb.nseg[m];
+    if (S == 0) return;  // merged by the compacted kernel
     unsigned *W = pb.W[dst] + 2 * lo;
     int *A = pb.A[dst] + 2 * lo, *B = pb.B[dst] + 2 * lo;
     int base = 0;
@@ -418,7 +420,7 @@ __global__ void k_seg_fallback(SegArgs a)
     const int64_t mid = lo + half, hi = (lo + 2 * half < G.n) ? lo + 2 * half : G.n;
     if (mid >= hi) return;
     const PassBufs &pb = a.pb[pass];
-    if (!a.sb[pass].nofit[m]) return;
+    if (!a.sb[pass].nofit[m] || a.sb[pass].nseg[m] == 0) return;
     const int src = (G.level - 1) & 1, dst = G.level & 1;
     GPts gp{ a.pts.P };
     GLinks lk{ pb.lk };
@@ -442,7 +444,7 @@ size_t seg_smem_bytes(int scap, int K) { return (size_t)scap * (sizeof(int4) + s
 void launch_seg_level(const Points &pts, int64_t n, int level, PassBufs *passes, SegBufs *sbufs, uint64_t *pairs,
                       uint32_t *pair_vals, uint64_t *pairs_alt, uint32_t *vals_alt, unsigned long long *npairs,
                       int *overflow, int64_t pair_cap, int64_t S_cap, int64_t M_cap, int K, int scap,
-                      const SortScratch &ss, int32_t *status, cudaStream_t st, int64_t *launches)
+                      int min_events, const SortScratch &ss, int32_t *status, cudaStream_t st, int64_t *launches)
 {
     SegArgs a;
     a.pts = pts;
@@ -453,6 +455,7 @@ void launch_seg_level(const Points &pts, int64_t n, int level, PassBufs *passes,
     a.geo.scap = scap;
     a.geo.ocap = 2 * K + 256;
     a.geo.pair_cap = pair_cap;
+    a.geo.min_events = min_events;
     a.pb[0] = passes[0];
     a.pb[1] = passes[1];
     a.sb[0] = sbufs[0];

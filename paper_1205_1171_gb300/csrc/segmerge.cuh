@@ -54,6 +54,7 @@ struct SegGeom {
     int scap;      // slot table capacity
     int ocap;      // output capacity per window
     int64_t pair_cap;
+    int min_events;  // merges with at most this many child events are not merged here
 };
 
 __host__ __device__ __forceinline__ int seg_count(int nl, int nr, int K, int smax)

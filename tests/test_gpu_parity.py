@@ -78,12 +78,13 @@ def test_upper_level_kernels_agree(H, cmp_level, cmp_slots):
         p.close()
 
 
-@pytest.mark.parametrize("seg_level,seg_events,seg_slots", [(2, 4, 64), (3, 16, 256), (6, 64, 2048), (9, 512, 2048),
-                                                            (4, 32, 40)])
-def test_segment_parallel_levels_agree(H, seg_level, seg_events, seg_slots):
+@pytest.mark.parametrize("seg_level,seg_events,seg_slots,seg_min", [(2, 4, 64, 1), (3, 16, 256, 1), (6, 64, 2048, 1),
+                                                                    (9, 512, 2048, 1), (4, 32, 40, 1), (3, 16, 256, 64)])
+def test_segment_parallel_levels_agree(H, seg_level, seg_events, seg_slots, seg_min):
     """Time-segment-parallel top levels (many windows per merge; tiny slot tables
-    force the serial fallback) give the oracle's faces."""
-    p = H.Hull3D(1 << 15, seg_level=seg_level, seg_events=seg_events, seg_slots=seg_slots)
+    force the retry table and the serial fallback; seg_min mixes in the
+    compacted kernel for small merges) give the oracle's faces."""
+    p = H.Hull3D(1 << 15, seg_level=seg_level, seg_events=seg_events, seg_slots=seg_slots, seg_min_events=seg_min)
     try:
         for dist in inputs.DISTS:
             for n in (3, 5, 77, 1000, 1 << 15):
@@ -179,17 +180,59 @@ def test_host_buffers_end_to_end(plan):
     assert np.array_equal(got, oracle.hull(pts))
 
 
-def test_batch_matches_single(H):
-    xyz, off, kinds = inputs.batch(40, 12, 4.0, 10.0)
-    p = H.Hull3D(len(xyz), max_clouds=40)
+def test_batch_matches_oracle(H):
+    xyz, off, kinds = inputs.batch(60, 12, 4.0, 12.0)
+    p = H.Hull3D(1 << 13, max_clouds=60)
     faces, foff, nf, st = p.batch(torch.from_numpy(xyz).cuda(), off)
     torch.cuda.synchronize()
     f = faces.cpu().numpy()
-    for b in range(40):
+    for b in range(60):
         assert st[b] == 0
         got = f[foff[b]: foff[b] + nf[b]]
         assert np.array_equal(got, oracle.hull(xyz[off[b]: off[b + 1]])), b
     p.close()
+
+
+def test_batch_all_classes_and_large_clouds_match_single_hulls(H):
+    """Every size class of the persistent kernel (<= 256, <= 1024, <= 4096
+    points), clouds above it (plain pipeline), degenerate and tiny clouds,
+    and per-cloud errors."""
+    rng = np.random.default_rng(4)
+    clouds = []
+    for i, n in enumerate([1, 2, 3, 4, 5, 16, 255, 256, 257, 1023, 1024, 1025, 4095, 4096, 4097, 9000, 20000]):
+        clouds.append(inputs.cloud_seeded(inputs.DISTS[i % 4], n, 900 + i))
+    clouds += _tiny_sets(40, 31)
+    g = np.array(np.meshgrid(*[np.arange(-3, 4)] * 3)).reshape(3, -1).T.astype(np.int32)
+    clouds.append(g)
+    bad_range = inputs.cloud_seeded("cube", 50, 1).copy()
+    bad_range[7, 2] = 1 << 20
+    dup = inputs.cloud_seeded("ball", 300, 2).copy()
+    dup[100] = dup[5]
+    clouds += [bad_range, dup]
+    order = rng.permutation(len(clouds))
+    clouds = [clouds[i] for i in order]
+    off = np.zeros(len(clouds) + 1, np.int64)
+    off[1:] = np.cumsum([len(c) for c in clouds])
+    xyz = np.concatenate(clouds).astype(np.int32)
+    p = H.Hull3D(1 << 15, max_clouds=len(clouds))
+    single = H.Hull3D(1 << 15)
+    try:
+        faces, foff, nf, st = p.batch(torch.from_numpy(xyz).cuda(), off)
+        torch.cuda.synchronize()
+        f = faces.cpu().numpy()
+        for b, c in enumerate(clouds):
+            x = torch.from_numpy(np.ascontiguousarray(c)).cuda()
+            try:
+                want = single.compute(x).cpu().numpy()
+                code = 0
+            except H.Hull3DError as e:
+                want, code = None, e.code
+            assert st[b] == code, (b, len(c), st[b], code)
+            if code == 0:
+                assert np.array_equal(f[foff[b]: foff[b] + nf[b]], want), (b, len(c))
+    finally:
+        p.close()
+        single.close()
 
 
 @pytest.mark.parametrize("dist", ["ball", "sphere"])
