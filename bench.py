@@ -161,6 +161,60 @@ def cpu_baseline_leg():
             "seconds": dt}
 
 
+BATCH_CLOUDS = 65536
+PLAIN_SAMPLE = 1024  # clouds timed through per-cloud plain launches
+
+
+def batched_leg(hull3d, torch, steps: int):
+    """65,536 independent clouds, sizes round(2^U(4, 12)), distribution drawn
+    per cloud: one persistent launch per size class vs per-cloud plain launches."""
+    from paper_1205_1171_gb300 import inputs
+
+    xyz, off, kinds = inputs.batch(BATCH_CLOUDS, inputs.seed_for(4))
+    sizes = np.diff(off)
+    caps = np.where(sizes >= 3, 2 * sizes - 4, 0)
+    foff = np.zeros(len(off), np.int64)
+    foff[1:] = np.cumsum(caps)
+    d_xyz = torch.from_numpy(xyz).cuda()
+    faces = torch.empty((int(foff[-1]), 3), dtype=torch.int32, device="cuda")
+    nf = torch.zeros(BATCH_CLOUDS, dtype=torch.int64, device="cuda")
+    st = torch.zeros(BATCH_CLOUDS, dtype=torch.int32, device="cuda")
+    plan = hull3d.Hull3D(4096, max_clouds=BATCH_CLOUDS)
+    stream = torch.cuda.current_stream()
+    plan.batch_async(d_xyz, off, faces, foff, nf, st, stream)
+    torch.cuda.synchronize()
+    assert int((st != 0).sum().item()) == 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        plan.batch_async(d_xyz, off, faces, foff, nf, st, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batch_ms = e0.elapsed_time(e1) / steps
+    launches = plan.last_launches
+    # per-cloud plain launches on a sample (a rate, so a sample measures it)
+    single = hull3d.Hull3D(4096, use_graph=-1)
+    pick = np.random.default_rng(0).choice(BATCH_CLOUDS, size=PLAIN_SAMPLE, replace=False)
+    views = [(d_xyz[off[b]: off[b + 1]], faces[foff[b]: foff[b + 1]] if caps[b] else faces[:1], nf[b: b + 1],
+              st[b: b + 1]) for b in pick]
+    for x, f, n1, s1 in views[:16]:
+        single.compute_async(x, f, n1, s1, stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for x, f, n1, s1 in views:
+        single.compute_async(x, f, n1, s1, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    plan.close()
+    single.close()
+    return {"workload": "65,536 clouds, sizes round(2^U(4,12)) (16..4096), distribution per cloud uniform over "
+                        "cube/ball/sphere/gauss", "points": int(len(xyz)),
+            "hulls_per_s": BATCH_CLOUDS / (batch_ms / 1e3), "ms_per_batch": batch_ms, "launches_per_batch": launches,
+            "per_cloud_plain_hulls_per_s": PLAIN_SAMPLE / (plain_ms / 1e3),
+            "per_cloud_plain_sample": PLAIN_SAMPLE}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -175,6 +229,7 @@ def main():
     ap.add_argument("--dists", default=",".join(DISTS), help="clouds per step (profiling runs only)")
     ap.add_argument("--seg-level", type=int, default=0, help="first time-segment-parallel level (0 = default)")
     ap.add_argument("--seg-events", type=int, default=0, help="child events per time window (0 = default)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 65,536-cloud batched measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     npts = args.n
@@ -293,6 +348,13 @@ def main():
                        "faces": nface, "l2": "inputs larger than L2 (201 MB per cloud), no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline}
+    if not args.no_batched:
+        b = batched_leg(hull3d, torch, max(1, args.steps // 2))
+        if dist:
+            t = torch.tensor([b["ms_per_batch"]], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            b["hulls_per_s"] = world * BATCH_CLOUDS / (float(t.item()) / 1e3)
+        line["batched"] = b
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_leg()
     if rank == 0:

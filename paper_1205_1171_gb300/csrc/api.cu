@@ -196,6 +196,11 @@ size_t layout(hull3d_plan_s *p, char *base)
             sb.ocnt = b.take<int>(p->S_cap);
             sb.bridge0 = b.take<int2>(p->M_cap);
             sb.nofit = b.take<int>(p->M_cap);
+            if (s == 0) {
+                sb.wlist = b.take<unsigned>(2 * p->S_cap);
+                sb.flist = b.take<unsigned>(2 * p->S_cap);
+                sb.mlist = b.take<unsigned>(2 * p->M_cap);
+            }
         }
         if (p->S_cap) {
             p->pk0 = b.take<uint64_t>(p->pair_cap);
@@ -203,7 +208,7 @@ size_t layout(hull3d_plan_s *p, char *base)
             p->pv0 = b.take<uint32_t>(p->pair_cap);
             p->pv1 = b.take<uint32_t>(p->pair_cap);
             p->npairs = b.take<unsigned long long>(1);
-            p->overflow = b.take<int>(1);
+            p->overflow = b.take<int>(4);  // pair overflow, merges in windows, windows, windows to retry
             // the pair sort needs histogram space for pair_cap items
             int64_t tiles = (p->pair_cap + SORT_TILE - 1) / SORT_TILE;
             if (tiles > p->ss.max_tiles) {
@@ -240,7 +245,7 @@ int default_cmp_slots(const hull3d_plan_s *p) { return p->opts.cmp_slots > 0 ? p
 int default_seg_level(const hull3d_plan_s *p) { return p->opts.seg_level > 0 ? p->opts.seg_level : 10; }
 int default_seg_min_events(const hull3d_plan_s *p)
 {
-    return p->opts.seg_min_events > 0 ? p->opts.seg_min_events : 4096;
+    return p->opts.seg_min_events > 0 ? p->opts.seg_min_events : 512;
 }
 int default_seg_events(const hull3d_plan_s *p) { return p->opts.seg_events > 0 ? p->opts.seg_events : 512; }
 int default_seg_slots(const hull3d_plan_s *p) { return p->opts.seg_slots > 0 ? p->opts.seg_slots : 1536; }
@@ -309,9 +314,12 @@ int enqueue_hull(hull3d_plan_s *p, const int32_t *d_xyz, int64_t n, int32_t *d_f
         int lv0 = -1, lv1 = -1;
         if (p->profile) { int r_ = mark(p, st, &lv0); if (r_) return r_; }
         if (seg) {
-            // small merges on the compacted warp kernel, large ones in time windows
+            // small merges on this level's usual kernel, large ones in time windows
             const int min_ev = default_seg_min_events(p);
-            launch_level_cmp(pts, n, level, p->pass, 2, status, st, default_cmp_slots(p), min_ev);
+            if (level >= default_cmp_level(p))
+                launch_level_cmp(pts, n, level, p->pass, 2, status, st, default_cmp_slots(p), min_ev);
+            else
+                launch_level(pts, n, level, p->pass, 2, status, st, default_occupancy(p, level), min_ev);
             launches++;
             launch_seg_level(pts, n, level, p->pass, p->seg, p->pk0, p->pv0, p->pk1, p->pv1, p->npairs, p->overflow,
                              p->pair_cap, p->S_cap, p->M_cap, default_seg_events(p), default_seg_slots(p), min_ev, p->ss,

@@ -276,10 +276,11 @@ void batch_kernel_attributes()
 {
     cudaFuncSetAttribute(k_batch<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BatchSmem<256>::bytes);
     cudaFuncSetAttribute(k_batch<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BatchSmem<1024>::bytes);
+    cudaFuncSetAttribute(k_batch<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BatchSmem<2048>::bytes);
     cudaFuncSetAttribute(k_batch<4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BatchSmem<4096>::bytes);
 }
 
-int batch_class_limit(int c) { return c == 0 ? 256 : c == 1 ? 1024 : 4096; }
+int batch_class_limit(int c) { return c == 0 ? 256 : c == 1 ? 1024 : c == 2 ? 2048 : 4096; }
 
 void launch_batch_class(int c, const int32_t *xyz, const int64_t *off, const int64_t *foff, const int32_t *order,
                         int count, int *counter, int32_t *faces, int64_t *nfaces, int32_t *status, int sms,
@@ -287,6 +288,7 @@ void launch_batch_class(int c, const int32_t *xyz, const int64_t *off, const int
 {
     if (c == 0) launch_class<256>(xyz, off, foff, order, count, counter, faces, nfaces, status, sms, st);
     else if (c == 1) launch_class<1024>(xyz, off, foff, order, count, counter, faces, nfaces, status, sms, st);
+    else if (c == 2) launch_class<2048>(xyz, off, foff, order, count, counter, faces, nfaces, status, sms, st);
     else launch_class<4096>(xyz, off, foff, order, count, counter, faces, nfaces, status, sms, st);
 }
 

@@ -50,9 +50,10 @@ void launch_level1(int64_t n, PassBufs *passes, int npass, int32_t *status, cuda
 void launch_fused(const Points &pts, int64_t n, int l0, int l1, PassBufs *passes, int npass, int32_t *status,
                   cudaStream_t st);
 
-// One level (>= 2), one thread per merge, global memory.
+// One level (>= 2), one thread per merge, global memory.  With max_events >= 0
+// only merges of at most max_events child events are done (see launch_level_cmp).
 void launch_level(const Points &pts, int64_t n, int level, PassBufs *passes, int npass, int32_t *status,
-                  cudaStream_t st, int occupancy);
+                  cudaStream_t st, int occupancy, int max_events = -1);
 
 // One level (>= 2), one warp per merge on a compacted shared-memory table of
 // up to scap slots (merges that do not fit run the global-memory merge).
@@ -91,10 +92,10 @@ void merge_kernel_attributes();
 void seg_kernel_attributes();
 void batch_kernel_attributes();
 
-// Batched clouds: size class c (0, 1, 2) holds clouds of at most
+// Batched clouds: size class c (0 .. BATCH_CLASSES - 1) holds clouds of at most
 // batch_class_limit(c) points; one persistent launch hulls `count` clouds
 // listed in order[] (cloud indices into off/foff), pulling work from *counter.
-constexpr int BATCH_CLASSES = 3;
+constexpr int BATCH_CLASSES = 4;
 int batch_class_limit(int c);
 void launch_batch_class(int c, const int32_t *xyz, const int64_t *off, const int64_t *foff, const int32_t *order,
                         int count, int *counter, int32_t *faces, int64_t *nfaces, int32_t *status, int sms,

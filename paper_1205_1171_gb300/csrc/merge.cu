@@ -47,7 +47,7 @@ void launch_level1(int64_t n, PassBufs *passes, int npass, int32_t *status, cuda
 // ---------------------------------------------------------------------------
 template <int MINB>
 __global__ void __launch_bounds__(128, MINB) k_level(Points pts, int64_t n, int level, PassBufs p0, PassBufs p1,
-                                                     int32_t *status)
+                                                     int max_events, int32_t *status)
 {
     if (*status) return;
     int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(128, MINB) k_level(Points pts, int64_t n, int 
     unsigned *Wdst = upper ? p1.W[dst] : p0.W[dst];
     int *Adst = upper ? p1.A[dst] : p0.A[dst], *Bdst = upper ? p1.B[dst] : p0.B[dst];
     int nl = csrc[lo], nr = csrc[mid];
+    if (max_events >= 0 && nl + nr > max_events) return;  // left to the time-segment kernels
     GPts gp{ pts.P };
     GLinks lk{ upper ? p1.lk : p0.lk };
     GEvIn L{ Wsrc + 2 * lo }, R{ Wsrc + 2 * mid };
@@ -95,14 +96,14 @@ __global__ void k_passthrough(int64_t lo, int level, PassBufs p0, PassBufs p1, i
 }
 
 void launch_level(const Points &pts, int64_t n, int level, PassBufs *passes, int npass, int32_t *status,
-                  cudaStream_t st, int occupancy)
+                  cudaStream_t st, int occupancy, int max_events)
 {
     int64_t nodes = (n + (1ll << level) - 1) >> level;
     dim3 g((unsigned)((nodes + 127) / 128), npass);
-    if (occupancy >= 4) k_level<4><<<g, 128, 0, st>>>(pts, n, level, passes[0], passes[npass - 1], status);
-    else k_level<1><<<g, 128, 0, st>>>(pts, n, level, passes[0], passes[npass - 1], status);
+    if (occupancy >= 4) k_level<4><<<g, 128, 0, st>>>(pts, n, level, passes[0], passes[npass - 1], max_events, status);
+    else k_level<1><<<g, 128, 0, st>>>(pts, n, level, passes[0], passes[npass - 1], max_events, status);
     int64_t lo = (nodes - 1) << level;
-    if (lo + (1ll << (level - 1)) >= n) launch_passthrough(n, level, lo, passes, status, st);
+    if (max_events < 0 && lo + (1ll << (level - 1)) >= n) launch_passthrough(n, level, lo, passes, status, st);
 }
 
 void launch_passthrough(int64_t n, int level, int64_t lo, PassBufs *passes, int32_t *status, cudaStream_t st)

@@ -15,6 +15,10 @@ struct SegArgs {
     uint32_t *pair_vals;
     unsigned long long *npairs;
     int *overflow;
+    int *nseg_merges;  // merges of this level that are merged in windows
+    // device work lists (entries: pass << 31 | index)
+    unsigned *wlist, *flist, *mlist;  // windows, windows to retry, merges in windows
+    int *wcount, *fcount;
     int64_t S_cap, M_cap;
     int32_t *status;
 };
@@ -39,9 +43,14 @@ __global__ void k_seg_bounds(SegArgs a)
     const int nl = pb.cnt[src][lo], nr = pb.cnt[src][mid];
     // small merges are done by the compacted kernel: no windows
     const int S = (nl + nr > G.min_events) ? seg_count(nl, nr, G.K, G.smax) : 0;
-    if (s == 0) { sb.nseg[m] = S; sb.nofit[m] = 0; }
+    if (s == 0) {
+        sb.nseg[m] = S;
+        sb.nofit[m] = 0;
+        if (S) a.mlist[atomicAdd(a.nseg_merges, 1)] = ((unsigned)pass << 31) | (unsigned)m;
+    }
     if (s >= S) return;
     const int64_t g = m * G.smax + s;
+    a.wlist[atomicAdd(a.wcount, 1)] = ((unsigned)pass << 31) | (unsigned)g;
     int kL = 0;
     const int j = (int)(((int64_t)s * (nl + nr)) / S);
     if (s > 0) {
@@ -83,25 +92,35 @@ __device__ __forceinline__ bool seg_locate(const SegGeom &G, const PassBufs &pb,
 // ---- idx: every event records its index under its point --------------------
 __global__ void k_seg_idx(SegArgs a)
 {
-    if (*a.status) return;
+    if (*a.status || *a.nseg_merges == 0) return;
     const int pass = blockIdx.y;
-    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int64_t clo, plo;
-    int k, E;
-    if (!seg_locate(a.geo, a.pb[pass], q, clo, plo, k, E)) return;
-    const unsigned w = a.pb[pass].W[(a.geo.level - 1) & 1][q];
-    const int rk = (int)(w & RANK_MASK);
-    if (w & INS_BIT) a.sb[pass].ins_idx[rk] = k;
-    else a.sb[pass].del_idx[rk] = k;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < 2 * a.geo.n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t clo, plo;
+        int k, E;
+        if (!seg_locate(a.geo, a.pb[pass], q, clo, plo, k, E)) continue;
+        const unsigned w = a.pb[pass].W[(a.geo.level - 1) & 1][q];
+        const int rk = (int)(w & RANK_MASK);
+        if (w & INS_BIT) a.sb[pass].ins_idx[rk] = k;
+        else a.sb[pass].del_idx[rk] = k;
+    }
 }
 
 // ---- pairs: each event point joins the start hulls of the windows it spans --
+__device__ void seg_pairs_one(const SegArgs &a, int pass, int64_t q);
+
 __global__ void k_seg_pairs(SegArgs a)
 {
-    if (*a.status) return;
+    if (*a.status || *a.nseg_merges == 0) return;
     const int pass = blockIdx.y;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < 2 * a.geo.n;
+         q += (int64_t)gridDim.x * blockDim.x)
+        seg_pairs_one(a, pass, q);
+}
+
+__device__ void seg_pairs_one(const SegArgs &a, int pass, int64_t q)
+{
     const SegGeom &G = a.geo;
-    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int64_t clo, plo;
     int k, E;
     const PassBufs &pb = a.pb[pass];
@@ -182,15 +201,28 @@ __device__ __forceinline__ int64_t lower_key(const uint64_t *keys, int64_t cnt, 
 // marks itself with ocnt = -1.  retry = 1: only those windows, with a table of
 // scap_big; a window that still does not fit sends its merge to the serial
 // fallback.
+__device__ void seg_window(const SegArgs &a, int pass, int64_t g, int retry, int scap_big);
+
 __global__ void __launch_bounds__(SEG_THREADS) k_seg_merge(SegArgs a, int retry, int scap_big)
+{
+    if (*a.status) return;
+    const unsigned *list = retry ? a.flist : a.wlist;
+    const int cnt = retry ? *a.fcount : *a.wcount;
+    for (int it = blockIdx.x; it < cnt; it += gridDim.x) {
+        const unsigned e = list[it];
+        seg_window(a, (int)(e >> 31), (int64_t)(e & 0x7fffffffu), retry, scap_big);
+        __syncthreads();
+    }
+}
+
+// One window: its start hulls and inserted points in a slot table, the start
+// bridge, the event loop.  All threads of the (one-warp) CTA call it.
+__device__ void seg_window(const SegArgs &a, int pass, int64_t g, int retry, int scap_big)
 {
     extern __shared__ int sm[];
     __shared__ int s_bad, s_nins;
-    if (*a.status) return;
-    const int pass = blockIdx.y;
     const bool upper = pass != 0;
     const SegGeom &G = a.geo;
-    const int64_t g = blockIdx.x;
     const int64_t m = g / G.smax;
     const int s = (int)(g % G.smax);
     const int64_t half = 1ll << (G.level - 1);
@@ -203,7 +235,6 @@ __global__ void __launch_bounds__(SEG_THREADS) k_seg_merge(SegArgs a, int retry,
     const int S = sb.nseg[m];
     if (s >= S) return;
     if (*a.overflow) { if (threadIdx.x == 0) sb.nofit[m] = 1; return; }
-    if (retry && sb.ocnt[g] != -1) return;
     const int scap = retry ? scap_big : G.scap;
     const int tid = threadIdx.x;
     const int src = (G.level - 1) & 1;
@@ -238,7 +269,7 @@ __global__ void __launch_bounds__(SEG_THREADS) k_seg_merge(SegArgs a, int retry,
     if (tsize > scap) {
         if (tid == 0) {
             if (retry) sb.nofit[m] = 1;
-            else sb.ocnt[g] = -1;
+            else a.flist[atomicAdd(a.fcount, 1)] = ((unsigned)pass << 31) | (unsigned)g;
         }
         return;
     }
@@ -350,13 +381,23 @@ __global__ void __launch_bounds__(SEG_THREADS) k_seg_merge(SegArgs a, int retry,
 // ---- concat: one CTA per merge ------------------------------------------------
 constexpr int CAT_THREADS = 256;
 
+__device__ void seg_concat_one(const SegArgs &a, int pass, int64_t m);
+
 __global__ void __launch_bounds__(CAT_THREADS) k_seg_concat(SegArgs a)
 {
-    __shared__ int s_off[CAT_THREADS + 1];
     if (*a.status) return;
-    const int pass = blockIdx.y;
+    const int cnt = *a.nseg_merges;
+    for (int it = blockIdx.x; it < cnt; it += gridDim.x) {
+        const unsigned e = a.mlist[it];
+        seg_concat_one(a, (int)(e >> 31), (int64_t)(e & 0x7fffffffu));
+        __syncthreads();
+    }
+}
+
+__device__ void seg_concat_one(const SegArgs &a, int pass, int64_t m)
+{
+    __shared__ int s_off[CAT_THREADS + 1];
     const SegGeom &G = a.geo;
-    const int64_t m = blockIdx.x;
     const int64_t half = 1ll << (G.level - 1);
     const int64_t lo = m << G.level;
     if (lo >= G.n) return;
@@ -411,9 +452,12 @@ __global__ void __launch_bounds__(CAT_THREADS) k_seg_concat(SegArgs a)
 __global__ void k_seg_fallback(SegArgs a)
 {
     if (*a.status) return;
-    const int pass = blockIdx.y;
+    const int it = blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= *a.nseg_merges) return;
+    const unsigned e = a.mlist[it];
+    const int pass = (int)(e >> 31);
     const SegGeom &G = a.geo;
-    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t m = (int64_t)(e & 0x7fffffffu);
     const int64_t half = 1ll << (G.level - 1);
     const int64_t lo = m << G.level;
     if (lo >= G.n) return;
@@ -467,13 +511,28 @@ void launch_seg_level(const Points &pts, int64_t n, int level, PassBufs *passes,
     a.status = status;
     const int64_t M = (n + (1ll << level) - 1) >> level;
     const int64_t G = M * a.geo.smax;
+    a.nseg_merges = overflow + 1;
+    a.wcount = overflow + 2;
+    a.fcount = overflow + 3;
+    a.wlist = sbufs[0].wlist;
+    a.flist = sbufs[0].flist;
+    a.mlist = sbufs[0].mlist;
     cudaMemsetAsync(npairs, 0, sizeof(unsigned long long), st);
-    cudaMemsetAsync(overflow, 0, sizeof(int), st);
+    cudaMemsetAsync(overflow, 0, 4 * sizeof(int), st);
     a.pairs = pairs;
     a.pair_vals = pair_vals;
     k_seg_bounds<<<dim3((unsigned)((G + 127) / 128), 2), 128, 0, st>>>(a);
-    k_seg_idx<<<dim3((unsigned)((2 * n + 255) / 256), 2), 256, 0, st>>>(a);
-    k_seg_pairs<<<dim3((unsigned)((2 * n + 255) / 256), 2), 256, 0, st>>>(a);
+    static int flat_grid = 0;
+    if (!flat_grid) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        flat_grid = sms > 0 ? 4 * sms : 512;
+    }
+    int64_t fg = (2 * n + 255) / 256;
+    if (fg > flat_grid) fg = flat_grid;
+    k_seg_idx<<<dim3((unsigned)fg, 2), 256, 0, st>>>(a);
+    k_seg_pairs<<<dim3((unsigned)fg, 2), 256, 0, st>>>(a);
     *launches += 3;
     int key_bits = 28;
     while ((1ll << (key_bits - 28)) < 4 * S_cap) key_bits++;
@@ -481,10 +540,14 @@ void launch_seg_level(const Points &pts, int64_t n, int level, PassBufs *passes,
                                  st, launches);
     a.pairs = which ? pairs_alt : pairs;
     a.pair_vals = which ? vals_alt : pair_vals;
-    k_seg_merge<<<dim3((unsigned)G, 2), SEG_THREADS, seg_smem_bytes(scap, K), st>>>(a, 0, scap);
-    k_seg_merge<<<dim3((unsigned)G, 2), SEG_THREADS, seg_smem_bytes(SEG_SLOTS_BIG, K), st>>>(a, 1, SEG_SLOTS_BIG);
-    k_seg_concat<<<dim3((unsigned)M, 2), CAT_THREADS, 0, st>>>(a);
-    k_seg_fallback<<<dim3((unsigned)((M + 31) / 32), 2), 32, 0, st>>>(a);
+    // persistent grids over the device work lists
+    const int wg = flat_grid * 2;  // about 8 one-warp CTAs per SM
+    k_seg_merge<<<wg, SEG_THREADS, seg_smem_bytes(scap, K), st>>>(a, 0, scap);
+    k_seg_merge<<<flat_grid / 4 > 0 ? flat_grid / 4 : 1, SEG_THREADS, seg_smem_bytes(SEG_SLOTS_BIG, K), st>>>(
+        a, 1, SEG_SLOTS_BIG);
+    k_seg_concat<<<flat_grid, CAT_THREADS, 0, st>>>(a);
+    const int64_t fb_threads = 2 * M;
+    k_seg_fallback<<<(unsigned)((fb_threads + 63) / 64), 64, 0, st>>>(a);
     *launches += 4;
     const int64_t last_lo = (M - 1) << level;
     if (last_lo + (1ll << (level - 1)) >= n) {

@@ -43,6 +43,7 @@ struct SegBufs {
     int *ocnt;              // [S_cap]
     int2 *bridge0;          // [M_cap]: t = -inf bridge (u0, v0) as ranks
     int *nofit;             // [M_cap]: 1 when a window did not fit (merge serially)
+    unsigned *wlist, *flist, *mlist;  // work lists (pass 0's copy holds both passes): [2 S_cap], [2 S_cap], [2 M_cap]
 };
 
 // Geometry of one segment level (shared by both passes).

@@ -70,21 +70,26 @@ __device__ __forceinline__ int64_t count_of(int64_t n, const int64_t *d_n)
     return c < n ? c : n;
 }
 
+// (grid-stride over the tiles in use, so a small device count costs little)
 __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t *__restrict__ keys, int64_t n,
                                                         const int64_t *d_n, int shift, uint32_t *hist, int64_t T)
 {
     __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
-    __syncthreads();
-    int64_t cnt = count_of(n, d_n);
-    int64_t base = blockIdx.x * (int64_t)SORT_TILE;
+    const int64_t cnt = count_of(n, d_n);
+    const int64_t Tu = (cnt + SORT_TILE - 1) / SORT_TILE;
+    for (int64_t tile = blockIdx.x; tile < Tu; tile += gridDim.x) {
+        h[threadIdx.x] = 0;
+        __syncthreads();
+        const int64_t base = tile * SORT_TILE;
 #pragma unroll 4
-    for (int it = 0; it < RS_ITEMS; it++) {
-        int64_t i = base + it * RS_THREADS + threadIdx.x;
-        if (i < cnt) atomicAdd(&h[(keys[i] >> shift) & 0xff], 1u);
+        for (int it = 0; it < RS_ITEMS; it++) {
+            int64_t i = base + it * RS_THREADS + threadIdx.x;
+            if (i < cnt) atomicAdd(&h[(keys[i] >> shift) & 0xff], 1u);
+        }
+        __syncthreads();
+        hist[threadIdx.x * T + tile] = h[threadIdx.x];
+        __syncthreads();
     }
-    __syncthreads();
-    hist[threadIdx.x * T + blockIdx.x] = h[threadIdx.x];
 }
 
 __global__ void __launch_bounds__(1024) k_rs_rowscan(uint32_t *hist, int64_t T, const int64_t *d_n, int64_t n,
@@ -138,10 +143,12 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *__res
 {
     __shared__ uint32_t dbase[256];
     __shared__ uint32_t wh[RS_WARPS][256];
-    int64_t cnt = count_of(n, d_n);
-    int64_t base = blockIdx.x * (int64_t)SORT_TILE;
-    if (base >= cnt) return;
+    __shared__ uint32_t ws[RS_WARPS];
+    const int64_t cnt = count_of(n, d_n);
+    const int64_t Tu = (cnt + SORT_TILE - 1) / SORT_TILE;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int64_t tile = blockIdx.x; tile < Tu; tile += gridDim.x) {
+    const int64_t base = tile * SORT_TILE;
 
     // digit bases: exclusive scan of the row totals, plus this tile's row prefix
     {
@@ -152,12 +159,11 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *__res
             uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
-        __shared__ uint32_t ws[RS_WARPS];
         if (lane == 31) ws[w] = x;
         __syncthreads();
         uint32_t off = 0;
         for (int k = 0; k < w; k++) off += ws[k];
-        dbase[tid] = off + x - v + hist[tid * T + blockIdx.x];
+        dbase[tid] = off + x - v + hist[tid * T + tile];
     }
 #pragma unroll
     for (int k = 0; k < RS_WARPS; k++) wh[k][tid] = 0;
@@ -202,6 +208,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *__res
         __syncwarp();
         if (dd[r] < 256) { kout[pos] = kk[r]; vout[pos] = vv[r]; }
     }
+    __syncthreads();
+    }
 }
 
 int radix_sort_pairs(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int64_t n, const int64_t *d_n,
@@ -210,13 +218,21 @@ int radix_sort_pairs(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int
     if (n <= 0) return 0;
     int64_t T = (n + SORT_TILE - 1) / SORT_TILE;
     int passes = (bits + 7) / 8;
+    static int grid_cap = 0;  // a few CTAs per SM: the kernels loop over the tiles in use
+    if (!grid_cap) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        grid_cap = sms > 0 ? 8 * sms : 1024;
+    }
+    const unsigned G = (unsigned)(T < grid_cap ? T : grid_cap);
     uint64_t *ka = k0, *kb = k1;
     uint32_t *va = v0, *vb = v1;
     for (int p = 0; p < passes; p++) {
         int shift = 8 * p;
-        k_rs_hist<<<(unsigned)T, RS_THREADS, 0, st>>>(ka, n, d_n, shift, s.hist, T);
+        k_rs_hist<<<G, RS_THREADS, 0, st>>>(ka, n, d_n, shift, s.hist, T);
         k_rs_rowscan<<<256, 1024, 0, st>>>(s.hist, T, d_n, n, s.rowsum);
-        k_rs_scatter<<<(unsigned)T, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, d_n, shift, s.hist, T, s.rowsum);
+        k_rs_scatter<<<G, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, d_n, shift, s.hist, T, s.rowsum);
         if (launches) *launches += 3;
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
