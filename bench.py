@@ -215,6 +215,56 @@ def batched_leg(hull3d, torch, steps: int):
             "per_cloud_plain_sample": PLAIN_SAMPLE}
 
 
+SERVE_RATE = 20000.0     # requests per second (Poisson)
+SERVE_SECONDS = 0.5      # arrival window measured
+SERVE_SERIAL = 1000      # arrivals replayed one request at a time for the comparison
+
+
+def serving_leg(hull3d, torch):
+    """Open-loop Poisson stream of hull requests, sizes round(2^U(6, 18)), mixed
+    distributions, 8 GB budget: continuous batching vs one request at a time."""
+    from paper_1205_1171_gb300 import serve
+
+    pool = serve.request_pool(256, inputs_seed(5))
+    arrivals = serve.poisson_arrivals(SERVE_RATE, SERVE_SECONDS, np.random.default_rng(6))
+    with serve.HullServer(budget_bytes=8 << 30) as srv:
+        warm = [srv.submit(c) for c in pool[:32]]
+        for f in warm:
+            f.result()
+        srv.stats = serve.Stats()
+        futs = serve.replay(srv.submit, arrivals, pool, np.random.default_rng(7))
+        for f in futs:
+            f.result()
+        served = srv.stats.summary()
+    plan = hull3d.Hull3D(1 << 18)
+    lat = []
+    picks = np.random.default_rng(7).integers(0, len(pool), size=len(arrivals))[:SERVE_SERIAL]
+    host = [torch.from_numpy(pool[k]).pin_memory() for k in range(len(pool))]
+    out = torch.empty((1 << 19, 3), dtype=torch.int32).pin_memory()
+    t0 = time.perf_counter()
+    for t, k in zip(arrivals[:SERVE_SERIAL], picks):
+        while time.perf_counter() < t0 + t:
+            pass
+        plan.compute_host(host[k], out)
+        lat.append(time.perf_counter() - (t0 + t))
+    span = time.perf_counter() - t0
+    plan.close()
+    lat = np.array(lat) * 1e3
+    pts = float(np.mean([len(pool[k]) for k in picks]))
+    return {"workload": f"Poisson {SERVE_RATE:.0f} req/s for {SERVE_SECONDS} s, sizes round(2^U(6,18)), mixed "
+                        "distributions, 8 GB budget, requests drawn from 256 distinct clouds",
+            "requests": int(len(arrivals)), "served": served,
+            "one_at_a_time": {"requests": int(len(lat)), "p50_ms": float(np.percentile(lat, 50)),
+                              "p99_ms": float(np.percentile(lat, 99)), "hulls_per_s": len(lat) / span},
+            "mean_points_per_request": pts}
+
+
+def inputs_seed(k: int) -> int:
+    from paper_1205_1171_gb300 import inputs
+
+    return inputs.seed_for(k)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -230,6 +280,7 @@ def main():
     ap.add_argument("--seg-level", type=int, default=0, help="first time-segment-parallel level (0 = default)")
     ap.add_argument("--seg-events", type=int, default=0, help="child events per time window (0 = default)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 65,536-cloud batched measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     npts = args.n
@@ -355,6 +406,8 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             b["hulls_per_s"] = world * BATCH_CLOUDS / (float(t.item()) / 1e3)
         line["batched"] = b
+    if not args.no_serving and rank == 0:
+        line["serving"] = serving_leg(hull3d, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_leg()
     if rank == 0:

@@ -143,6 +143,18 @@ class Hull3D:
         self._plan = plan
         self.max_n = int(max_n)
 
+    @classmethod
+    def tuned(cls, max_n: int, max_clouds: int = 0, cache: str | None = None, **overrides):
+        """A plan with the knobs the autotuner stored for this GPU and size (the
+        library defaults when nothing was tuned); explicit overrides win."""
+        import torch
+
+        from paper_1205_1171_gb300 import autotune
+
+        knobs = autotune.lookup(torch.cuda.get_device_name(), max_n, cache or autotune.DEFAULT_CACHE) or {}
+        knobs.update(overrides)
+        return cls(max_n, max_clouds, **knobs)
+
     def close(self):
         if getattr(self, "_plan", None):
             self._lib.hull3d_destroy(self._plan)
