@@ -104,7 +104,7 @@ class CudaBackend:
         self.large_slots = []
         for _ in range(large_slots):
             self.large_slots.append({
-                "plan": hull3d.Hull3D(large_max),
+                "plan": hull3d.Hull3D(large_max, use_graph=-1),  # sizes vary: no graph re-capture per request
                 "stream": torch.cuda.Stream(dev),
                 "xyz": torch.empty((large_max, 3), dtype=torch.int32, device=dev),
                 "faces": torch.empty((2 * large_max, 3), dtype=torch.int32, device=dev),
