@@ -45,6 +45,32 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# DRAM bytes (read + write) per launch of the thread-per-merge level kernel,
+# from one ncu capture of the n = 2^24 cube + Gaussian step (the command and
+# the per-level figures are in profiles/), valid for the merge sources whose
+# SHA-256 is recorded with it.
+KERNEL_TRAFFIC = {"bytes_per_launch": 7870788201, "sources_sha256": "c4e6154a5b4b5d665369c0eabfe96ba586c32d3774e7b090122c0d19c323921e"}
+TRAFFIC_SOURCES = ("paper_1205_1171_gb300/csrc/merge.cu", "paper_1205_1171_gb300/csrc/merge.cuh",
+                   "paper_1205_1171_gb300/csrc/predicates.cuh")
+
+
+def sources_sha256() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for rel in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def kernel_traffic():
+    """The recorded DRAM traffic per launch, or None once the kernel changed."""
+    if not KERNEL_TRAFFIC or KERNEL_TRAFFIC["sources_sha256"] != sources_sha256():
+        return None
+    return KERNEL_TRAFFIC["bytes_per_launch"]
+
+
 def make_inputs(rank: int, n: int = N_POINTS, dists=DISTS):
     from paper_1205_1171_gb300 import inputs
 
@@ -105,15 +131,26 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def alg_bytes(n: int, ev: np.ndarray, fused_l1: int, nfaces: int) -> dict:
-    """Algorithmic bytes per call and phase (the definitions are in the design doc)."""
+def level_alg_bytes(n: int, ev: np.ndarray, level: int) -> int:
+    """Algorithmic bytes of merge level `level`, both passes: 4 B per child and
+    per parent event (an event is one int32 rank) and 12 B per point whose
+    coordinates the merges read.  Those points are the child event points and
+    the four x-extremes of each merge, so E(level - 1) + 4 M bounds them."""
+    half = 1 << (level - 1)
+    merges = (n >> level) + (1 if n % (1 << level) > half else 0)
+    return sum(4 * (int(ev[p, level - 1]) + int(ev[p, level])) + 12 * (int(ev[p, level - 1]) + 4 * merges)
+               for p in range(2))
+
+
+def alg_bytes(n: int, ev: np.ndarray, fused_l1: int, nfaces: int, seg_level: int) -> dict:
+    """Algorithmic bytes per call and phase: read the input (12 n) and write the
+    sorted points (16 n); the merge levels; 12 B per output face."""
     L = int(np.ceil(np.log2(n)))
     l1 = min(fused_l1, L)
-    out = {"sort": 28 * n, "fused": 16 * n, "levels": 0, "seg": 0, "faces": 72 * nfaces}
-    for p in range(2):
-        out["fused"] += 8 * n + 12 * int(ev[p, l1])
-        for lv in range(l1 + 1, L + 1):
-            out["levels"] += 20 * int(ev[p, lv - 1]) + 12 * int(ev[p, lv])
+    out = {"sort": 28 * n, "fused": 0, "levels": 0, "seg": 0, "faces": 12 * nfaces}
+    for lv in range(2, L + 1):
+        phase = "fused" if lv <= l1 else ("seg" if lv >= seg_level else "levels")
+        out[phase] += level_alg_bytes(n, ev, lv)
     return out
 
 
@@ -348,6 +385,7 @@ def main():
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
     clk = clocks.stop()
+    level_ms = plan.profile_levels()
     phase_ms, calls = plan.profile_read()
     plan.profile(False)
     if dist:
@@ -380,17 +418,28 @@ def main():
     e2e = {"value": points / e_dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": 12 * npts * len(clouds),
            "d2h_bytes_per_step": d2h // args.steps}
 
-    # roofline of the dominant phase, from the phase events recorded live in the timed region
+    # roofline of the dominant kernel -- the thread-per-merge level kernel, which
+    # runs the levels below the compacted ones -- from the per-level events
+    # recorded live on the launching stream in the timed region
     peak, peak_kind = peaks()
-    ab = [alg_bytes(npts, ev, plan.fused_levels_used, nf) for ev, nf in zip(level_ev, nface)]
+    o = plan.opts
+    steps = max(args.steps, 1)
+    L = int(np.ceil(np.log2(npts)))
+    klev = [lv for lv in range(plan.fused_levels_used + 1, L + 1) if lv < o["cmp_level"]]
+    k_bytes = sum(level_alg_bytes(npts, ev, lv) for ev in level_ev for lv in klev)  # per step
+    k_ms = sum(float(level_ms[lv]) for lv in klev) / steps
+    k_launches = len(klev) * len(clouds)
+    achieved = k_bytes / (k_ms / 1e3) / 1e9 if k_ms > 0 else 0.0
+    ab = [alg_bytes(npts, ev, plan.fused_levels_used, nf, o["seg_level"]) for ev, nf in zip(level_ev, nface)]
     alg = {k: sum(a[k] for a in ab) for k in ab[0]}  # bytes per step
-    dom = max(phase_ms, key=lambda k: phase_ms[k])
-    per_step_ms = phase_ms[dom] / max(args.steps, 1)
-    achieved = alg[dom] / (per_step_ms / 1e3) / 1e9 if per_step_ms > 0 else 0.0
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "phase": dom, "peak_kind": peak_kind,
-                "phase_ms_per_step": {k: v / max(args.steps, 1) for k, v in phase_ms.items()},
-                "alg_bytes_per_step": alg}
+                "traffic": kernel_traffic(), "kernel": "k_level (one thread per merge)",
+                "levels": [klev[0], klev[-1]] if klev else [], "launches_per_step": k_launches,
+                "alg_bytes_per_launch": k_bytes / max(k_launches, 1), "ms_per_launch": k_ms / max(k_launches, 1),
+                "peak_kind": peak_kind,
+                "phase_ms_per_step": {k: v / steps for k, v in phase_ms.items()},
+                "phase_alg_bytes_per_step": alg,
+                "phase_gbs": {k: alg[k] / (phase_ms[k] / steps / 1e3) / 1e9 for k in alg if phase_ms[k] > 0}}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
