@@ -71,6 +71,17 @@ def kernel_traffic():
     return KERNEL_TRAFFIC["bytes_per_launch"]
 
 
+def max_over_ranks(x: float, dist, device: str = "cuda") -> float:
+    """The largest x over the ranks (every rank gets it); x itself without a process group."""
+    if not dist:
+        return x
+    import torch
+
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_inputs(rank: int, n: int = N_POINTS, dists=DISTS):
     from paper_1205_1171_gb300 import inputs
 
@@ -388,10 +399,8 @@ def main():
     level_ms = plan.profile_levels()
     phase_ms, calls = plan.profile_read()
     plan.profile(False)
+    ms = max_over_ranks(ms, dist)
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     points = len(clouds) * npts * args.steps * world
     value = points / (ms / 1e3) / 1e6
@@ -411,10 +420,7 @@ def main():
             f = plan.compute_host(x, host_out)
             d2h += f.shape[0] * 12 + 12
     e_dt = time.perf_counter() - e0
-    if dist:
-        t = torch.tensor([e_dt], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_dt = float(t.item())
+    e_dt = max_over_ranks(e_dt, dist)
     e2e = {"value": points / e_dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": 12 * npts * len(clouds),
            "d2h_bytes_per_step": d2h // args.steps}
 
@@ -451,9 +457,7 @@ def main():
     if not args.no_batched:
         b = batched_leg(hull3d, torch, max(1, args.steps // 2))
         if dist:
-            t = torch.tensor([b["ms_per_batch"]], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            b["hulls_per_s"] = world * BATCH_CLOUDS / (float(t.item()) / 1e3)
+            b["hulls_per_s"] = world * BATCH_CLOUDS / (max_over_ranks(b["ms_per_batch"], dist) / 1e3)
         line["batched"] = b
     if not args.no_serving and rank == 0:
         line["serving"] = serving_leg(hull3d, torch)

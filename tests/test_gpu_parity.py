@@ -264,3 +264,41 @@ def test_graph_replay_matches_plain_launches(H):
     finally:
         g.close()
         plain.close()
+
+
+def _golden():
+    import json
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_hulls.json")
+    with open(path) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("name", ["cube_2e24", "gauss_2e24", "ball_2e20", "sphere_2e20"])
+def test_full_size_matches_stored_oracle_digest(H, name):
+    """The full-size clouds, in the launch configuration bench.py times (one
+    plan of 2^24 points with the default knobs, graph replay through
+    hull3d_compute_async), against the oracle's face count and face-list
+    digest stored by tests/golden/make_oracle_hulls.py."""
+    import hashlib
+
+    g = _golden().get(name)
+    if g is None:
+        pytest.skip(f"no stored oracle digest for {name}")
+    pts = inputs.cloud_seeded(g["dist"], g["n"], g["seed"])
+    p = H.Hull3D(1 << 24)
+    try:
+        x = torch.from_numpy(pts).cuda()
+        faces = torch.empty((2 * g["n"], 3), dtype=torch.int32, device="cuda")
+        nf = torch.zeros(1, dtype=torch.int64, device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        for _ in range(2):  # the first call captures the graph, the second replays it
+            p.compute_async(x, faces, nf, st)
+            torch.cuda.synchronize()
+            assert int(st.item()) == 0
+            got = faces[: int(nf.item())].cpu().numpy()
+            assert got.shape[0] == g["faces"]
+            assert hashlib.sha256(np.ascontiguousarray(got, dtype="<i4").tobytes()).hexdigest() == g["sha256"]
+    finally:
+        p.close()
