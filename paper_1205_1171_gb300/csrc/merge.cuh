@@ -198,6 +198,102 @@ __device__ int kinetic_forward(const PT &pt, LK &lk, int &u, int &v, Tri old, bo
     return k;
 }
 
+// The same forward pass with the six candidates in a CTA's shared memory
+// instead of a per-thread array.  The loop indexes the candidates at run
+// time, so an array lives in local memory, and with hundreds of resident
+// threads per SM those accesses miss L1 and become most of the kernel's
+// memory traffic; a shared-memory slice per thread, field-major so that the
+// threads of a warp hit distinct banks, keeps them on chip.
+struct CandSmem {
+    int *I;        // [4][6][T]: p, q, r, s
+    long long *Q;  // [3][6][T]: Z, Y, Nx
+    int T, t;
+    __device__ __forceinline__ int &fi(int f, int l) const { return I[(f * 6 + l) * T + t]; }
+    __device__ __forceinline__ long long &fq(int f, int l) const { return Q[(f * 6 + l) * T + t]; }
+    __device__ __forceinline__ Tri get(int l) const
+    {
+        Tri x;
+        x.p = fi(0, l); x.q = fi(1, l); x.r = fi(2, l); x.s = fi(3, l);
+        x.Z = fq(0, l); x.Y = fq(1, l); x.Nx = fq(2, l);
+        return x;
+    }
+    __device__ __forceinline__ void set(int l, const Tri &x) const
+    {
+        fi(0, l) = x.p; fi(1, l) = x.q; fi(2, l) = x.r; fi(3, l) = x.s;
+        fq(0, l) = x.Z; fq(1, l) = x.Y; fq(2, l) = x.Nx;
+    }
+};
+// shared-memory bytes of CandSmem for a CTA of T threads
+constexpr int cand_smem_bytes(int T) { return T * 6 * (4 * 4 + 3 * 8); }
+
+template <class PT, class LK, class EIN, class EOUT>
+__device__ int kinetic_forward_sm(const PT &pt, LK &lk, int &u, int &v, const EIN &L, int nl, const EIN &R, int nr,
+                                  EOUT &out, int cap, bool upper, int *err, const CandSmem &c)
+{
+    unsigned valid = 0;  // bit l: candidate l is finite and later than the last event
+#pragma unroll
+    for (int l = 0; l < 6; l++) c.fi(0, l) = c.fi(1, l) = c.fi(2, l) = -2;  // no triple yet
+    Tri old;
+    bool have_old = false;
+    int i = 0, j = 0, k = 0;
+    for (;;) {
+        const int e0 = i < nl ? (int)(L.w(i) & RANK_MASK) : NIL;
+        const int e1 = j < nr ? (int)(R.w(j) & RANK_MASK) : NIL;
+        const int2 l0 = e0 >= 0 ? lk.get(e0) : make_int2(NIL, NIL);
+        const int2 l1 = e1 >= 0 ? lk.get(e1) : make_int2(NIL, NIL);
+        const int2 lu = lk.get(u), lv = lk.get(v);
+        // refresh the candidates whose triple changed (as in kinetic_forward)
+#pragma unroll 1
+        for (int l = 0; l < 6; l++) {
+            int tp, tq, tr;
+            switch (l) {
+            case 0: tp = l0.x; tq = e0; tr = l0.y; break;
+            case 1: tp = l1.x; tq = e1; tr = l1.y; break;
+            case 2: tp = u; tq = lu.y; tr = v; break;
+            case 3: tp = lu.x; tq = u; tr = v; break;
+            case 4: tp = u; tq = lv.x; tr = v; break;
+            default: tp = u; tq = v; tr = lv.y; break;
+            }
+            if (tp != c.fi(0, l) || tq != c.fi(1, l) || tr != c.fi(2, l)) {
+                Tri t;
+                tri_make(pt, t, tp, tq, tr);
+                c.set(l, t);
+                bool ok = t.s != 0 && (!have_old || tri_cmp(pt, t, old, upper) > 0);
+                valid = ok ? (valid | (1u << l)) : (valid & ~(1u << l));
+            }
+        }
+        int best = -1;
+        Tri t;
+#pragma unroll 1
+        for (int l = 0; l < 6; l++) {
+            if (!((valid >> l) & 1u)) continue;
+            const Tri cl = c.get(l);
+            if (best < 0 || tri_cmp(pt, cl, t, upper) < 0) { best = l; t = cl; }
+        }
+        if (best < 0) break;
+        if (k >= cap) { *err = 1; return cap; }
+        if (best <= 1) {
+            const int e = t.q;
+            bool vis;
+            if (best == 0) { i++; vis = pt.rk(e) < pt.rk(u); }
+            else { j++; vis = pt.rk(e) > pt.rk(v); }
+            if (vis) out.put(k++, (unsigned)e | (lk.nxt(t.p) != e ? INS_BIT : 0u), t.p, t.r);
+            act(lk, e);
+        } else {
+            const bool ins = (best == 2) | (best == 4);
+            out.put(k++, (unsigned)t.q | (ins ? INS_BIT : 0u), t.p, t.r);
+            if (best == 2) u = t.q;
+            else if (best == 3) u = t.p;
+            else if (best == 4) v = t.q;
+            else v = t.r;
+        }
+        old = t;
+        have_old = true;
+        valid &= ~(1u << best);
+    }
+    return k;
+}
+
 #ifdef __CUDACC__
 __device__ __forceinline__ Tri shfl_tri(const Tri &t, int src, unsigned mask = 0xffffffffu)
 {
@@ -353,6 +449,19 @@ __device__ int kinetic_merge(const PT &pt, LK &lk, int u0, int v0, int mid, cons
     int k = kinetic_forward(pt, lk, u, v, none, false, L, nl, R, nr, out, cap, upper, false, err);  // 2.
     if (k >= cap && *err) return k;
     kinetic_backward(pt, lk, u, v, mid, out, k);  // 3.
+    return k;
+}
+
+// kinetic_merge with the candidates of the event loop in shared memory.
+template <class PT, class LK, class EIN, class EOUT>
+__device__ int kinetic_merge_sm(const PT &pt, LK &lk, int u0, int v0, int mid, const EIN &L, int nl, const EIN &R,
+                                int nr, EOUT &out, int cap, bool upper, int *err, const CandSmem &cs)
+{
+    int u = u0, v = v0;
+    bridge_walk(pt, lk, u, v, (const Tri *)nullptr, upper);
+    int k = kinetic_forward_sm(pt, lk, u, v, L, nl, R, nr, out, cap, upper, err, cs);
+    if (k >= cap && *err) return k;
+    kinetic_backward(pt, lk, u, v, mid, out, k);
     return k;
 }
 
