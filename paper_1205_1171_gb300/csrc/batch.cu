@@ -91,8 +91,17 @@ struct BatchSmem {
     static constexpr size_t bytes = (size_t)A_BYTES + sizeof(int4) * NMAX + sizeof(int2) * NMAX;
 };
 
+// CTAs of a class that fit in an SM's 228 KB of shared memory (at most 4):
+// the register cap follows, so a class that cannot have more resident CTAs
+// does not pay for a tighter cap with spills.
 template <int NMAX>
-__global__ void __launch_bounds__(BATCH_THREADS, 4) k_batch(const int32_t *__restrict__ xyz,
+constexpr int batch_ctas_per_sm()
+{
+    return (int)((233472 / (BatchSmem<NMAX>::bytes + 1024)) < 4 ? (233472 / (BatchSmem<NMAX>::bytes + 1024)) : 4);
+}
+
+template <int NMAX>
+__global__ void __launch_bounds__(BATCH_THREADS, batch_ctas_per_sm<NMAX>()) k_batch(const int32_t *__restrict__ xyz,
                                                          const int64_t *__restrict__ off,
                                                          const int64_t *__restrict__ foff,
                                                          const int32_t *__restrict__ order, int count, int *counter,

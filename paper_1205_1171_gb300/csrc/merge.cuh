@@ -55,17 +55,21 @@ __device__ __forceinline__ void tri_make(const PT &pt, Tri &t, int p, int q, int
     else t.s = turn_slow(P, Q, R);
 }
 
-// The tie tiers of tri_cmp (unperturbed times equal), out of line.
+// The tie tiers of tri_cmp (unperturbed times equal), out of line.  The
+// triples come by value, field by field: an argument passed by reference
+// would make the caller keep its copy of the triple in local memory.
 template <class PT>
-__device__ __noinline__ int tri_cmp_tie(const PT &pt, const Tri &a, const Tri &b)
+__device__ __noinline__ int tri_cmp_tie(PT pt, int ap, int aq, int ar, int as, long long aZ, long long aY,
+                                        long long aNx, int bp, int bq, int br, int bs, long long bZ, long long bY,
+                                        long long bNx)
 {
-    if (a.p == b.p && a.q == b.q && a.r == b.r) return 0;
+    if (ap == bp && aq == bq && ar == br) return 0;
     // shear tiers: -c.z then -c.y with c = N1 x N2, N = (Nx, -Z, Y)
-    i128 cz = (i128)a.Z * b.Nx - (i128)a.Nx * b.Z;
-    if (cz != 0) return -sgn128(cz) * a.s * b.s;
-    i128 cy = (i128)a.Y * b.Nx - (i128)a.Nx * b.Y;
-    if (cy != 0) return -sgn128(cy) * a.s * b.s;
-    return time_cmp_index(pt, a.p, a.q, a.r, b.p, b.q, b.r, a.s * b.s);
+    i128 cz = (i128)aZ * bNx - (i128)aNx * bZ;
+    if (cz != 0) return -sgn128(cz) * as * bs;
+    i128 cy = (i128)aY * bNx - (i128)aNx * bY;
+    if (cy != 0) return -sgn128(cy) * as * bs;
+    return time_cmp_index(pt, ap, aq, ar, bp, bq, br, as * bs);
 }
 
 // sign(t(a) - t(b)) in the pass's time direction, both finite.
@@ -73,7 +77,8 @@ template <class PT>
 __device__ __forceinline__ int tri_cmp(const PT &pt, const Tri &a, const Tri &b, bool upper)
 {
     i128 D0 = (i128)a.Z * b.Y - (i128)b.Z * a.Y;
-    int s = D0 != 0 ? sgn128(D0) * a.s * b.s : tri_cmp_tie(pt, a, b);
+    int s = D0 != 0 ? sgn128(D0) * a.s * b.s
+                    : tri_cmp_tie(pt, a.p, a.q, a.r, a.s, a.Z, a.Y, a.Nx, b.p, b.q, b.r, b.s, b.Z, b.Y, b.Nx);
     return upper ? -s : s;
 }
 

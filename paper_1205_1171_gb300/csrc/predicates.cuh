@@ -58,7 +58,7 @@ __device__ __forceinline__ void zy3(const P3 &p, const P3 &q, const P3 &r, long 
 }
 
 // sign of Y~(p, q, r): nonzero for distinct points.
-static __device__ __noinline__ int turn_slow(const P3 &p, const P3 &q, const P3 &r)
+static __device__ __noinline__ int turn_slow(P3 p, P3 q, P3 r)
 {
     long long nx, ny, nz;
     normal3(p, q, r, nx, ny, nz);
@@ -127,7 +127,7 @@ __device__ __forceinline__ long long ww_coef(const long long u[3], const long lo
 // gam_i then gam_i eta_j coefficients, indices ascending.  ss = sign(Y~A) sign(Y~B).
 // Returns 0 only for equal point sets.
 template <class PT>
-__device__ __noinline__ int time_cmp_index(const PT &pt, int a0, int a1, int a2, int b0, int b1, int b2, int ss)
+__device__ __noinline__ int time_cmp_index(PT pt, int a0, int a1, int a2, int b0, int b1, int b2, int ss)
 {
     const P3 A[3] = { pt.get(a0), pt.get(a1), pt.get(a2) };
     const P3 B[3] = { pt.get(b0), pt.get(b1), pt.get(b2) };
