@@ -149,6 +149,19 @@ static void pt_zt(Poly *r, const Pt *p) /* z~ = z + gam_id */
     poly_add_term(r, 0, 0, p->id, -1, 1);
 }
 
+/* The same coordinates with b, every gam and every eta set to zero: only the
+ * shear infinitesimal a is kept. */
+static void pt_yt_a(Poly *r, const Pt *p) /* y~ with b = eta = 0 */
+{
+    r->n = 0;
+    poly_add_term(r, 0, 0, -1, -1, p->y);
+}
+static void pt_zt_a(Poly *r, const Pt *p) /* z~ with gam = 0 */
+{
+    r->n = 0;
+    poly_add_term(r, 0, 0, -1, -1, p->z);
+}
+
 typedef void (*coord_fn)(Poly *, const Pt *);
 
 /* 2D cross product of the (x~, w~) projections: (q-p) x (r-p), w~ = y~ or z~ */
@@ -171,6 +184,13 @@ static int turn_sign(const Pt *p, const Pt *q, const Pt *r)
     int64_t nz = (q->x - p->x) * (r->y - p->y) - (r->x - p->x) * (q->y - p->y);
     if (nz) return sgn64(nz);
     static _Thread_local Poly Yt;
+    /* Lazy evaluation of the same polynomial: setting b, gam, eta to zero keeps
+     * exactly its pure-a monomials, and any of those outranks every monomial
+     * that contains b, a gam or an eta; so when that part is not zero its
+     * leading sign is the answer. */
+    poly_cross2(&Yt, p, q, r, pt_yt_a);
+    int sa = poly_lead_sign(&Yt);
+    if (sa) return sa;
     poly_cross2(&Yt, p, q, r, pt_yt);
     return poly_lead_sign(&Yt);
 }
@@ -205,6 +225,16 @@ static int time_cmp_pts(const Pt *T1[3], const Pt *T2[3])
     i128 D0 = (i128)Z1 * Y2 - (i128)Z2 * Y1;
     if (D0) return sgn128(D0) * s1 * s2;
     static _Thread_local Poly Zt1, Yt1, Zt2, Yt2, m1, m2, D;
+    /* the pure-a part of D first (see turn_sign): it decides unless it is zero */
+    poly_cross2(&Zt1, T1[0], T1[1], T1[2], pt_zt_a);
+    poly_cross2(&Yt1, T1[0], T1[1], T1[2], pt_yt_a);
+    poly_cross2(&Zt2, T2[0], T2[1], T2[2], pt_zt_a);
+    poly_cross2(&Yt2, T2[0], T2[1], T2[2], pt_yt_a);
+    poly_mul(&m1, &Zt1, &Yt2);
+    poly_mul(&m2, &Zt2, &Yt1);
+    poly_sub(&D, &m1, &m2);
+    int sa = poly_lead_sign(&D);
+    if (sa) return sa * s1 * s2;
     poly_cross2(&Zt1, T1[0], T1[1], T1[2], pt_zt);
     poly_cross2(&Yt1, T1[0], T1[1], T1[2], pt_yt);
     poly_cross2(&Zt2, T2[0], T2[1], T2[2], pt_zt);
