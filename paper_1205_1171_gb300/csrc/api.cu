@@ -182,7 +182,11 @@ size_t layout(hull3d_plan_s *p, char *base)
             if (M > p->M_cap) p->M_cap = M;
         }
         const int64_t ocap = 2 * K + 256;
-        p->pair_cap = p->S_cap ? 4 * N + 8 * p->S_cap : 0;
+        // start-hull entries of one level: windows x (the two child hull sizes).
+        // Points on a sphere are the worst case of the workloads: its child hulls
+        // hold ~0.8 sqrt(m) points, so the top levels of a 2^20-point sphere need
+        // ~4.7 n entries; beyond the budget a level's windowed merges run serially.
+        p->pair_cap = p->S_cap ? 8 * N + 8 * p->S_cap : 0;
         for (int s = 0; s < 2 && p->S_cap; s++) {
             SegBufs &sb = p->seg[s];
             sb.bound = b.take<int2>(p->S_cap);
@@ -231,13 +235,16 @@ size_t layout(hull3d_plan_s *p, char *base)
     return b.off;
 }
 
-// Defaults from the measured level sweep (2^24 cube and clipped Gaussian, GB300):
-// no fused bottom kernel, the 128-register thread-per-merge kernel up to level
-// 9, the uncapped one for levels 10-12, the compacted warp kernel from 13 on.
+// Defaults from the measured level sweeps (2^24 cube and clipped Gaussian,
+// GB300): no fused bottom kernel; the thread-per-merge kernel with 128
+// registers (4 blocks per SM) up to level 9 except levels 6-7, where 168
+// registers (3 blocks) are faster, and uncapped for levels 10-12; the
+// compacted warp kernel from level 13 on.
 int default_fused(const hull3d_plan_s *p) { return p->opts.fused_levels > 0 ? p->opts.fused_levels : 1; }
 int default_occupancy(const hull3d_plan_s *p, int level)
 {
     if (p->opts.level_occupancy > 0) return p->opts.level_occupancy;
+    if (level == 6 || level == 7) return 3;
     return level <= 9 ? 4 : 1;
 }
 int default_cmp_level(const hull3d_plan_s *p) { return p->opts.cmp_level > 0 ? p->opts.cmp_level : 13; }

@@ -45,9 +45,9 @@ void launch_level1(int64_t n, PassBufs *passes, int npass, int32_t *status, cuda
 // ---------------------------------------------------------------------------
 // One level in global memory, one thread per merge.
 // ---------------------------------------------------------------------------
-// SMC: the event loop's candidates live in shared memory (cand_smem_bytes of
+// The event loop's candidates live in shared memory (cand_smem_bytes of
 // dynamic shared memory) rather than in a per-thread local array.
-template <int MINB, bool SMC>
+template <int MINB>
 __global__ void __launch_bounds__(128, MINB) k_level(Points pts, int64_t n, int level, PassBufs p0, PassBufs p1,
                                                      int max_events, int32_t *status)
 {
@@ -72,16 +72,10 @@ __global__ void __launch_bounds__(128, MINB) k_level(Points pts, int64_t n, int 
     GEvIn L{ Wsrc + 2 * lo }, R{ Wsrc + 2 * mid };
     GEvOut out{ Wdst + 2 * lo, Adst + 2 * lo, Bdst + 2 * lo };
     int err = 0;
-    int k;
-    if (SMC) {
-        extern __shared__ long long cand_sm[];  // the block's event-loop candidates
-        const CandSmem cs{ (int *)(cand_sm + 3 * 6 * blockDim.x), cand_sm, (int)blockDim.x, (int)threadIdx.x };
-        k = kinetic_merge_sm(gp, lk, (int)mid - 1, (int)mid, (int)mid, L, nl, R, nr, out, (int)(2 * (hi - lo)), upper,
-                             &err, cs);
-    } else {
-        k = kinetic_merge(gp, lk, (int)mid - 1, (int)mid, (int)mid, L, nl, R, nr, out, (int)(2 * (hi - lo)), upper,
-                          &err);
-    }
+    extern __shared__ long long cand_sm[];  // the block's event-loop candidates
+    const CandSmem cs{ (int *)(cand_sm + 3 * 6 * blockDim.x), cand_sm, (int)blockDim.x, (int)threadIdx.x };
+    const int k = kinetic_merge_sm(gp, lk, (int)mid - 1, (int)mid, (int)mid, L, nl, R, nr, out, (int)(2 * (hi - lo)),
+                                   upper, &err, cs);
     cdst[lo] = k;
     if (err) set_status2(status, HULL3D_ERR_INTERNAL);
     atomicAdd((upper ? p1.lev_events : p0.lev_events) + level, (unsigned long long)k);
@@ -111,17 +105,13 @@ void launch_level(const Points &pts, int64_t n, int level, PassBufs *passes, int
 {
     int64_t nodes = (n + (1ll << level) - 1) >> level;
     dim3 g((unsigned)((nodes + 127) / 128), npass);
-    // level 2 (4-point merges of event-free pairs) is faster with the local array
     const int sm = cand_smem_bytes(128);
     const Points &P = pts;
     PassBufs &a = passes[0], &b = passes[npass - 1];
-    if (level <= 2) {
-        if (occupancy >= 4) k_level<4, false><<<g, 128, 0, st>>>(P, n, level, a, b, max_events, status);
-        else k_level<1, false><<<g, 128, 0, st>>>(P, n, level, a, b, max_events, status);
-    } else {
-        if (occupancy >= 4) k_level<4, true><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, status);
-        else k_level<1, true><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, status);
-    }
+    if (occupancy >= 4) k_level<4><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, status);
+    else if (occupancy == 3) k_level<3><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, status);
+    else if (occupancy == 2) k_level<2><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, status);
+    else k_level<1><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, status);
     int64_t lo = (nodes - 1) << level;
     if (max_events < 0 && lo + (1ll << (level - 1)) >= n) launch_passthrough(n, level, lo, passes, status, st);
 }

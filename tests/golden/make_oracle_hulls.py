@@ -39,22 +39,25 @@ def face_digest(faces: np.ndarray) -> str:
 
 def main(names):
     oracle.build()
-    try:
-        with open(OUT) as f:
-            table = json.load(f)
-    except (OSError, ValueError):
-        table = {}
     for name in names:
         dist, n, seed = CASES[name]
         pts = inputs.cloud_seeded(dist, n, seed)
         t0 = time.time()
         faces = oracle.hull(pts)
-        table[name] = {"dist": dist, "n": n, "seed": seed, "faces": int(faces.shape[0]),
-                       "sha256": face_digest(faces), "oracle_seconds": round(time.time() - t0, 1)}
-        print(name, table[name], flush=True)
-        with open(OUT + ".tmp", "w") as f:
+        entry = {"dist": dist, "n": n, "seed": seed, "faces": int(faces.shape[0]), "sha256": face_digest(faces),
+                 "oracle_seconds": round(time.time() - t0, 1)}
+        print(name, entry, flush=True)
+        # re-read just before writing: several cases may run as separate processes
+        try:
+            with open(OUT) as f:
+                table = json.load(f)
+        except (OSError, ValueError):
+            table = {}
+        table[name] = entry
+        tmp = f"{OUT}.tmp{os.getpid()}"
+        with open(tmp, "w") as f:
             json.dump(table, f, indent=1, sort_keys=True)
-        os.replace(OUT + ".tmp", OUT)
+        os.replace(tmp, OUT)
 
 
 if __name__ == "__main__":

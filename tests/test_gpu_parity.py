@@ -237,13 +237,24 @@ def test_batch_all_classes_and_large_clouds_match_single_hulls(H):
 
 @pytest.mark.parametrize("dist", ["ball", "sphere"])
 def test_2e20_bit_exact(H, dist):
-    """The 2^20-point configurations (ball: few hull points; sphere: ~2n faces)."""
+    """The 2^20-point configurations (ball: few hull points; sphere: ~2n faces)
+    in a plan of exactly their size.  The plan's start-hull budget covers the
+    sphere's top levels, so no level falls back to serial merging: the hull
+    takes ~0.1 s (a fallback made it ~3.5 s)."""
+    import time
+
     pts = inputs.cloud_seeded(dist, 1 << 20, inputs.seed_for(2))
     p = H.Hull3D(1 << 20)
-    got = p.compute(torch.from_numpy(pts).cuda()).cpu().numpy()
+    x = torch.from_numpy(pts).cuda()
+    p.compute(x)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    got = p.compute(x).cpu().numpy()
+    dt = time.perf_counter() - t0
     p.close()
     want = oracle.hull(pts)
     assert np.array_equal(got, want)
+    assert dt < 1.0, f"{dist} 2^20 took {dt:.2f} s"
 
 
 def test_graph_replay_matches_plain_launches(H):
