@@ -149,17 +149,18 @@ static void pt_zt(Poly *r, const Pt *p) /* z~ = z + gam_id */
     poly_add_term(r, 0, 0, p->id, -1, 1);
 }
 
-/* The same coordinates with b, every gam and every eta set to zero: only the
- * shear infinitesimal a is kept. */
-static void pt_yt_a(Poly *r, const Pt *p) /* y~ with b = eta = 0 */
+/* The pure-a part of a predicate: set b, every gam and every eta to zero, so
+ * that x~ = x + a z + a^2 y is a polynomial in a alone (coefficients (x, z, y))
+ * while y~ = y and z~ = z.  The 2D cross product (q-p) x (r-p) of the
+ * (x~, w) projections is then a polynomial of degree 2 in a; out[k] is its
+ * coefficient of a^k (|out[k]| < 2^43). */
+static void cross2_a(int64_t out[3], const Pt *p, const Pt *q, const Pt *r, int w_is_z)
 {
-    r->n = 0;
-    poly_add_term(r, 0, 0, -1, -1, p->y);
-}
-static void pt_zt_a(Poly *r, const Pt *p) /* z~ with gam = 0 */
-{
-    r->n = 0;
-    poly_add_term(r, 0, 0, -1, -1, p->z);
+    const int64_t dxq[3] = { q->x - p->x, q->z - p->z, q->y - p->y };
+    const int64_t dxr[3] = { r->x - p->x, r->z - p->z, r->y - p->y };
+    const int64_t dwq = w_is_z ? q->z - p->z : q->y - p->y;
+    const int64_t dwr = w_is_z ? r->z - p->z : r->y - p->y;
+    for (int k = 0; k < 3; k++) out[k] = dxq[k] * dwr - dxr[k] * dwq;
 }
 
 typedef void (*coord_fn)(Poly *, const Pt *);
@@ -183,14 +184,15 @@ static int turn_sign(const Pt *p, const Pt *q, const Pt *r)
 {
     int64_t nz = (q->x - p->x) * (r->y - p->y) - (r->x - p->x) * (q->y - p->y);
     if (nz) return sgn64(nz);
-    static _Thread_local Poly Yt;
     /* Lazy evaluation of the same polynomial: setting b, gam, eta to zero keeps
      * exactly its pure-a monomials, and any of those outranks every monomial
-     * that contains b, a gam or an eta; so when that part is not zero its
-     * leading sign is the answer. */
-    poly_cross2(&Yt, p, q, r, pt_yt_a);
-    int sa = poly_lead_sign(&Yt);
-    if (sa) return sa;
+     * that contains b, a gam or an eta (smaller powers of a rank higher); so
+     * when that part is not zero its lowest nonzero coefficient decides. */
+    int64_t ya[3];
+    cross2_a(ya, p, q, r, 0);
+    for (int k = 1; k < 3; k++)
+        if (ya[k]) return sgn64(ya[k]);
+    static _Thread_local Poly Yt;
     poly_cross2(&Yt, p, q, r, pt_yt);
     return poly_lead_sign(&Yt);
 }
@@ -224,17 +226,26 @@ static int time_cmp_pts(const Pt *T1[3], const Pt *T2[3])
     cross_zy(T2[0], T2[1], T2[2], &Z2, &Y2);
     i128 D0 = (i128)Z1 * Y2 - (i128)Z2 * Y1;
     if (D0) return sgn128(D0) * s1 * s2;
+    /* the pure-a part of D first (see turn_sign): with Z~ and Y~ of degree 2 in
+     * a, D = Z~1 Y~2 - Z~2 Y~1 has degree 4 (|coefficients| < 2^88); its
+     * lowest nonzero coefficient decides unless all of them are zero */
+    {
+        int64_t z1[3], y1[3], z2[3], y2[3];
+        cross2_a(z1, T1[0], T1[1], T1[2], 1);
+        cross2_a(y1, T1[0], T1[1], T1[2], 0);
+        cross2_a(z2, T2[0], T2[1], T2[2], 1);
+        cross2_a(y2, T2[0], T2[1], T2[2], 0);
+        for (int k = 1; k <= 4; k++) {
+            i128 d = 0;
+            for (int i = 0; i <= 2; i++) {
+                int j = k - i;
+                if (j < 0 || j > 2) continue;
+                d += (i128)z1[i] * y2[j] - (i128)z2[i] * y1[j];
+            }
+            if (d) return sgn128(d) * s1 * s2;
+        }
+    }
     static _Thread_local Poly Zt1, Yt1, Zt2, Yt2, m1, m2, D;
-    /* the pure-a part of D first (see turn_sign): it decides unless it is zero */
-    poly_cross2(&Zt1, T1[0], T1[1], T1[2], pt_zt_a);
-    poly_cross2(&Yt1, T1[0], T1[1], T1[2], pt_yt_a);
-    poly_cross2(&Zt2, T2[0], T2[1], T2[2], pt_zt_a);
-    poly_cross2(&Yt2, T2[0], T2[1], T2[2], pt_yt_a);
-    poly_mul(&m1, &Zt1, &Yt2);
-    poly_mul(&m2, &Zt2, &Yt1);
-    poly_sub(&D, &m1, &m2);
-    int sa = poly_lead_sign(&D);
-    if (sa) return sa * s1 * s2;
     poly_cross2(&Zt1, T1[0], T1[1], T1[2], pt_zt);
     poly_cross2(&Yt1, T1[0], T1[1], T1[2], pt_yt);
     poly_cross2(&Zt2, T2[0], T2[1], T2[2], pt_zt);

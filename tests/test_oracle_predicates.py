@@ -180,3 +180,26 @@ def test_time_cmp_plain_rationals_in_general_position():
         done += 1
         want = 1 if t[0] > t[1] else -1
         assert oracle.time_cmp(p.astype(np.int32), np.arange(6, dtype=np.int32)) == want
+
+
+def test_equal_x_ties_at_full_coordinate_range():
+    """Triples through a pair of points with equal x tie at the unperturbed
+    level for every third point (their time is that of the pair); at 2^24
+    points in [-2^20, 2^20)^3 most points share their x with others, so this is
+    the tie the oracle resolves most often.  Cases where the shear terms decide
+    and, with equal x and z (or x and y) as well, where deeper terms must."""
+    rng = np.random.default_rng(11)
+    for it in range(240):
+        p = rng.integers(-(1 << 20), 1 << 20, size=(4, 3))
+        p[1, 0] = p[0, 0]  # p0, p1 share x
+        if it % 3 == 1:
+            p[1, 2] = p[0, 2]  # ... and z
+        elif it % 3 == 2:
+            p[1, 1] = p[0, 1]  # ... and y
+        if not _distinct(p):
+            continue
+        ids = rng.permutation(50)[:4].astype(np.int32)
+        q = p[[0, 1, 2, 0, 1, 3]].astype(np.int32)
+        j = ids[[0, 1, 2, 0, 1, 3]]
+        assert oracle.time_cmp(q, j) == ref_time_cmp(q, j), (q.tolist(), j.tolist())
+        assert oracle.turn_sign(q[:3], j[:3]) == ref_turn(q[:3], j[:3]), (q.tolist(), j.tolist())
