@@ -67,7 +67,9 @@ typedef struct {
     int32_t cmp_slots;       /* its shared-memory table size in points (<= 4096) */
     int32_t seg_slots;       /* shared-memory table size of one time window in points (<= 6144) */
     int32_t seg_min_events;  /* from seg_level on, merges with fewer child events use the compacted kernel */
-    int32_t reserved[7];
+    int32_t merge_order;     /* thread-per-merge levels 3-8 run their merges longest first: 1 (default),
+                                or in x-order: -1 */
+    int32_t reserved[6];
 } hull3d_opts;
 
 /* Creates a plan for hulls of up to max_n points (hull3d_compute*) and for

@@ -50,10 +50,20 @@ void launch_level1(int64_t n, PassBufs *passes, int npass, int32_t *status, cuda
 void launch_fused(const Points &pts, int64_t n, int l0, int l1, PassBufs *passes, int npass, int32_t *status,
                   cudaStream_t st);
 
+// Scratch for sorting a level's merges by their work (the point-sort buffers,
+// free while the levels run).
+struct LevelOrder {
+    uint64_t *k0, *k1;
+    uint32_t *v0, *v1;
+    SortScratch ss;
+};
+
 // One level (>= 2), one thread per merge, global memory.  With max_events >= 0
 // only merges of at most max_events child events are done (see launch_level_cmp).
-void launch_level(const Points &pts, int64_t n, int level, PassBufs *passes, int npass, int32_t *status,
-                  cudaStream_t st, int occupancy, int max_events = -1);
+// With ord, the merges of both passes run in order of decreasing child event
+// count.  Returns the number of kernel launches.
+int launch_level(const Points &pts, int64_t n, int level, PassBufs *passes, int npass, int32_t *status,
+                 cudaStream_t st, int occupancy, int max_events = -1, const LevelOrder *ord = nullptr);
 
 // One level (>= 2), one warp per merge on a compacted shared-memory table of
 // up to scap slots (merges that do not fit run the global-memory merge).

@@ -47,15 +47,48 @@ void launch_level1(int64_t n, PassBufs *passes, int npass, int32_t *status, cuda
 // ---------------------------------------------------------------------------
 // The event loop's candidates live in shared memory (cand_smem_bytes of
 // dynamic shared memory) rather than in a per-thread local array.
+// Merge order of one level: the (pass, node) entries sorted by the merge's
+// child event count, longest first.  In x-order, neighbouring merges take
+// quite different numbers of rounds and a warp runs as long as its longest
+// merge (about 70% of the lanes busy on a uniform cube); sorted, the 32 merges
+// of a warp take about as many rounds each.
+__global__ void k_order_keys(int64_t n, int level, PassBufs p0, PassBufs p1, int64_t nodes, uint64_t *keys,
+                             uint32_t *vals)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= 2 * nodes) return;
+    const int pass = i >= nodes ? 1 : 0;
+    const int64_t node = pass ? i - nodes : i;
+    const int src = (level - 1) & 1;
+    const int64_t lo = node << level, mid = lo + (1ll << (level - 1));
+    unsigned work = 0;  // a node without a right child sorts last (k_level skips it)
+    if (mid < n) {
+        const int *c = (pass ? p1 : p0).cnt[src];
+        const unsigned w = (unsigned)c[lo] + (unsigned)c[mid];
+        work = (w < 0xfffeu ? w : 0xfffeu) + 1;
+    }
+    keys[i] = 0xffffu - work;
+    vals[i] = ((uint32_t)pass << 31) | (uint32_t)node;
+}
+
+// order == nullptr: merge (pass = blockIdx.y, node = thread index); else the
+// thread's entry of the sorted merge order.
 template <int MINB>
 __global__ void __launch_bounds__(128, MINB) k_level(Points pts, int64_t n, int level, PassBufs p0, PassBufs p1,
-                                                     int max_events, int32_t *status)
+                                                     int max_events, const uint32_t *order, int64_t entries,
+                                                     int32_t *status)
 {
     if (*status) return;
     int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool upper = blockIdx.y != 0;
+    if (order) {
+        if (node >= entries) return;
+        const uint32_t e = order[node];
+        upper = (e >> 31) != 0;
+        node = e & 0x7fffffffu;
+    }
     int64_t lo = node << level;
     if (lo >= n) return;
-    const bool upper = blockIdx.y != 0;
     const int src = (level - 1) & 1, dst = level & 1;
     const int64_t half = 1ll << (level - 1);
     const int64_t mid = lo + half, hi = (lo + 2 * half < n) ? lo + 2 * half : n;
@@ -100,20 +133,38 @@ __global__ void k_passthrough(int64_t lo, int level, PassBufs p0, PassBufs p1, i
     if (blockIdx.x == 0 && threadIdx.x == 0) (up ? p1.cnt[dst] : p0.cnt[dst])[lo] = c;
 }
 
-void launch_level(const Points &pts, int64_t n, int level, PassBufs *passes, int npass, int32_t *status,
-                  cudaStream_t st, int occupancy, int max_events)
+int launch_level(const Points &pts, int64_t n, int level, PassBufs *passes, int npass, int32_t *status,
+                 cudaStream_t st, int occupancy, int max_events, const LevelOrder *ord)
 {
+    int launches = 0;
     int64_t nodes = (n + (1ll << level) - 1) >> level;
     dim3 g((unsigned)((nodes + 127) / 128), npass);
+    const uint32_t *order = nullptr;
+    int64_t entries = 0;
+    if (ord && npass == 2) {
+        entries = 2 * nodes;
+        k_order_keys<<<(unsigned)((entries + 255) / 256), 256, 0, st>>>(n, level, passes[0], passes[1], nodes,
+                                                                         ord->k0, ord->v0);
+        int64_t sl = 0;
+        const int which = radix_sort_pairs(ord->k0, ord->v0, ord->k1, ord->v1, entries, nullptr, 16, ord->ss, st, &sl);
+        launches += 1 + (int)sl;
+        order = which ? ord->v1 : ord->v0;
+        g = dim3((unsigned)((entries + 127) / 128), 1);
+    }
     const int sm = cand_smem_bytes(128);
     const Points &P = pts;
     PassBufs &a = passes[0], &b = passes[npass - 1];
-    if (occupancy >= 4) k_level<4><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, status);
-    else if (occupancy == 3) k_level<3><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, status);
-    else if (occupancy == 2) k_level<2><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, status);
-    else k_level<1><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, status);
+    if (occupancy >= 4) k_level<4><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, order, entries, status);
+    else if (occupancy == 3) k_level<3><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, order, entries, status);
+    else if (occupancy == 2) k_level<2><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, order, entries, status);
+    else k_level<1><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, order, entries, status);
+    launches++;
     int64_t lo = (nodes - 1) << level;
-    if (max_events < 0 && lo + (1ll << (level - 1)) >= n) launch_passthrough(n, level, lo, passes, status, st);
+    if (max_events < 0 && lo + (1ll << (level - 1)) >= n) {
+        launch_passthrough(n, level, lo, passes, status, st);
+        launches++;
+    }
+    return launches;
 }
 
 void launch_passthrough(int64_t n, int level, int64_t lo, PassBufs *passes, int32_t *status, cudaStream_t st)

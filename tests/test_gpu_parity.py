@@ -96,6 +96,22 @@ def test_segment_parallel_levels_agree(H, seg_level, seg_events, seg_slots, seg_
         p.close()
 
 
+@pytest.mark.parametrize("merge_order,occ", [(1, 4), (-1, 4), (1, 3), (1, 1)])
+def test_merge_order_and_register_caps_agree(H, merge_order, occ):
+    """Merges of a level run longest first or in x-order, at every register
+    cap of the thread-per-merge kernel, with the same faces."""
+    p = H.Hull3D(1 << 15, merge_order=merge_order, level_occupancy=occ, cmp_level=99, seg_level=64)
+    try:
+        for dist in inputs.DISTS:
+            for n in (3, 5, 77, 1000, 3001, 1 << 15):
+                pts = inputs.cloud_seeded(dist, n, 8100 + n + occ)
+                assert np.array_equal(run(p, pts), oracle.hull(pts)), (dist, n)
+        for pts in _tiny_sets(100, 37):
+            assert np.array_equal(run(p, pts), oracle.hull(pts)), pts.tolist()
+    finally:
+        p.close()
+
+
 def test_config_small_cube_4096(plan):
     pts = inputs.cloud_seeded("cube", 4096, inputs.seed_for(1))
     got = run(plan, pts)
