@@ -80,7 +80,7 @@ class CudaBackend:
     """GPU work through the C ABI: batch slots and a pool of large-cloud plans."""
 
     def __init__(self, small_max: int = 4096, batch_points: int = 1 << 21, batch_clouds: int = 8192,
-                 large_slots: int = 4, large_max: int = 1 << 18, device: str = "cuda"):
+                 large_slots: int = 8, large_max: int = 1 << 18, device: str = "cuda"):
         import torch
 
         from paper_1205_1171_gb300 import hull3d
