@@ -63,7 +63,8 @@ typedef struct {
     int32_t seg_events;      /* target child events per time window of a segment-parallel merge */
     int32_t use_graph;       /* 1: replay the level sequence as a CUDA graph, -1: plain launches */
     int32_t level_occupancy; /* thread-per-merge kernel: 128-thread blocks per SM its register cap allows (1 = no cap .. 4) */
-    int32_t cmp_level;       /* first level merged by the compacted warp-per-merge kernel */
+    int32_t cmp_level;       /* first level merged by the compacted warp-per-merge kernel (automatic:
+                                log2 n - 11 within [6, 13] for a hull of n points) */
     int32_t cmp_slots;       /* its shared-memory table size in points (<= 4096) */
     int32_t seg_slots;       /* shared-memory table size of one time window in points (<= 6144) */
     int32_t seg_min_events;  /* from seg_level on, merges with fewer child events use the compacted kernel */

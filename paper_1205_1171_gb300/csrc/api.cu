@@ -247,7 +247,17 @@ int default_occupancy(const hull3d_plan_s *p, int level)
     if (level == 6 || level == 7) return 3;
     return level <= 9 ? 4 : 1;
 }
-int default_cmp_level(const hull3d_plan_s *p) { return p->opts.cmp_level > 0 ? p->opts.cmp_level : 13; }
+// First level of the compacted warp-per-merge kernel for a hull of 2^L points
+// (L = ceil(log2 n)): one thread per merge pays while a level has enough merges
+// to fill the GPU, one warp per merge after that.  log2(n) - 11, within [6, 13],
+// was at or within 1% of the best cut-over measured for every n from 2^12 to
+// 2^24 (cube, ball, sphere, clipped Gaussian).
+int default_cmp_level(const hull3d_plan_s *p, int L)
+{
+    if (p->opts.cmp_level > 0) return p->opts.cmp_level;
+    const int c = L - 11;
+    return c < 6 ? 6 : (c > 13 ? 13 : c);
+}
 int default_cmp_slots(const hull3d_plan_s *p) { return p->opts.cmp_slots > 0 ? p->opts.cmp_slots : 1024; }
 int default_seg_level(const hull3d_plan_s *p) { return p->opts.seg_level > 0 ? p->opts.seg_level : 10; }
 int default_seg_min_events(const hull3d_plan_s *p)
@@ -332,7 +342,7 @@ int enqueue_hull(hull3d_plan_s *p, const int32_t *d_xyz, int64_t n, int32_t *d_f
         if (seg) {
             // small merges on this level's usual kernel, large ones in time windows
             const int min_ev = default_seg_min_events(p);
-            if (level >= default_cmp_level(p)) {
+            if (level >= default_cmp_level(p, L)) {
                 launch_level_cmp(pts, n, level, p->pass, 2, status, st, default_cmp_slots(p), min_ev);
                 launches++;
             } else {
@@ -343,7 +353,7 @@ int enqueue_hull(hull3d_plan_s *p, const int32_t *d_xyz, int64_t n, int32_t *d_f
                              p->pair_cap, p->S_cap, p->M_cap, default_seg_events(p), default_seg_slots(p), min_ev, p->ss,
                              status, st, &launches);
         } else {
-            if (level >= default_cmp_level(p)) {
+            if (level >= default_cmp_level(p, L)) {
                 launch_level_cmp(pts, n, level, p->pass, 2, status, st, default_cmp_slots(p));
                 int64_t last_lo = (((n + (1ll << level) - 1) >> level) - 1) << level;
                 launches += (last_lo + (1ll << (level - 1)) >= n) ? 2 : 1;  // level + pass-through copy
@@ -491,7 +501,7 @@ int hull3d_plan_opts(hull3d_plan_t p, hull3d_opts *out)
     *out = p->opts;
     out->fused_levels = default_fused(p);
     out->level_occupancy = p->opts.level_occupancy;
-    out->cmp_level = default_cmp_level(p);
+    out->cmp_level = default_cmp_level(p, ceil_log2(p->max_n));
     out->cmp_slots = default_cmp_slots(p);
     out->seg_level = default_seg_level(p);
     out->seg_events = default_seg_events(p);
