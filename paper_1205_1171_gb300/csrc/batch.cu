@@ -20,6 +20,15 @@
 namespace hull3d {
 
 constexpr int BATCH_THREADS = 128;
+// Threads per CTA of a size class.  The 4096 class fits one cloud per SM
+// (shared memory), so it takes 256 threads: twice the warps for its
+// warp-per-merge levels (measured on the 65,536-cloud batch: that class 733 ->
+// 582 ms; 512 threads spill at the register cap they imply and are slower).
+template <int NMAX>
+constexpr int batch_threads()
+{
+    return NMAX >= 4096 ? 256 : BATCH_THREADS;
+}
 
 struct BEvIn {
     const unsigned *W;
@@ -101,7 +110,7 @@ constexpr int batch_ctas_per_sm()
 }
 
 template <int NMAX>
-__global__ void __launch_bounds__(BATCH_THREADS, batch_ctas_per_sm<NMAX>()) k_batch(const int32_t *__restrict__ xyz,
+__global__ void __launch_bounds__(batch_threads<NMAX>(), batch_ctas_per_sm<NMAX>()) k_batch(const int32_t *__restrict__ xyz,
                                                          const int64_t *__restrict__ off,
                                                          const int64_t *__restrict__ foff,
                                                          const int32_t *__restrict__ order, int count, int *counter,
@@ -194,7 +203,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, batch_ctas_per_sm<NMAX>()) k_ba
                             if (err) s_err = HULL3D_ERR_INTERNAL;
                         }
                     } else {  // one warp per merge, warp-cooperative rounds
-                        for (int t = warp; t < nodes; t += BATCH_THREADS / 32) {
+                        for (int t = warp; t < nodes; t += batch_threads<NMAX>() / 32) {
                             const int llo = t * 2 * half, lmid = llo + half, lhi = min(llo + 2 * half, n);
                             if (lmid >= lhi) {
                                 const int c = Csrc[llo];
@@ -274,11 +283,12 @@ static void launch_class(const int32_t *xyz, const int64_t *off, const int64_t *
     if (count <= 0) return;
     const size_t smem = BatchSmem<NMAX>::bytes;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<NMAX>, BATCH_THREADS, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<NMAX>, batch_threads<NMAX>(), smem);
     if (per_sm < 1) per_sm = 1;
     int grid = sms * per_sm;
     if (grid > count) grid = count;
-    k_batch<NMAX><<<grid, BATCH_THREADS, smem, st>>>(xyz, off, foff, order, count, counter, faces, nfaces, status);
+    k_batch<NMAX><<<grid, batch_threads<NMAX>(), smem, st>>>(xyz, off, foff, order, count, counter, faces, nfaces,
+                                                             status);
 }
 
 void batch_kernel_attributes()
