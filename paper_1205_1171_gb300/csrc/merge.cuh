@@ -347,17 +347,28 @@ __device__ int kinetic_forward_warp(const PT &pt, LK &lk, int &u, int &v, Tri ol
                 valid = c.s != 0 && (!have_old || tri_cmp(pt, c, old, upper) > 0);
             }
         }
-        int bi = (lane < 6 && valid) ? lane : -1;
-        Tri bt = c;
+        // all 15 pairs at once: lane k < 15 compares candidates (i, j) = pair k;
+        // the earliest valid candidate is the one that beats the other five
+        // (equal triples: the lower index wins, as in the serial scan)
+        const int pk = lane < 15 ? lane : 0;
+        const int pi = pk < 5 ? 0 : pk < 9 ? 1 : pk < 12 ? 2 : pk < 14 ? 3 : 4;
+        const int pj = pk - (pi == 0 ? -1 : pi == 1 ? 3 : pi == 2 ? 6 : pi == 3 ? 8 : 9);
+        const Tri ti = shfl_tri(c, pi), tj = shfl_tri(c, pj);
+        const bool vi = __shfl_sync(FULL, valid, pi) != 0, vj = __shfl_sync(FULL, valid, pj) != 0;
+        const bool ibeats = lane < 15 && vi && (!vj || tri_cmp(pt, ti, tj, upper) <= 0);
+        const unsigned win = __ballot_sync(FULL, ibeats);
+        const unsigned vmask = __ballot_sync(FULL, lane < 6 && valid) & 0x3fu;
+        int best = -1;
+        if (vmask) {
+            // pair bits where candidate x is the first (I) or second (J) member
+            constexpr unsigned IM[6] = { 0x001fu, 0x01e0u, 0x0e00u, 0x3000u, 0x4000u, 0x0000u };
+            constexpr unsigned JM[6] = { 0x0000u, 0x0001u, 0x0022u, 0x0244u, 0x1488u, 0x6910u };
 #pragma unroll
-        for (int off = 4; off >= 1; off >>= 1) {
-            const int oi = __shfl_down_sync(FULL, bi, off);
-            const Tri ot = shfl_tri(bt, (lane + off) & 31);
-            if (lane < 8 && oi >= 0 && (bi < 0 || tri_cmp(pt, ot, bt, upper) < 0)) { bi = oi; bt = ot; }
+            for (int x = 0; x < 6; x++)
+                if (((vmask >> x) & 1u) && (win & IM[x]) == IM[x] && (win & JM[x]) == 0) best = x;
         }
-        const int best = __shfl_sync(FULL, bi, 0);
         if (best < 0) break;
-        const Tri t = shfl_tri(bt, 0);
+        const Tri t = shfl_tri(c, best);
         if (k >= cap) { *err = 1; return cap; }
         if (best <= 1) {
             const int e = t.q;
