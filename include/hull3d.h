@@ -60,7 +60,7 @@ typedef struct hull3d_plan_s *hull3d_plan_t;
 typedef struct {
     int32_t fused_levels;    /* bottom levels merged in one shared-memory kernel (1 = none, up to 10) */
     int32_t seg_level;       /* first level merged time-segment-parallel (> log2 n: never) */
-    int32_t seg_events;      /* target child events per time window of a segment-parallel merge */
+    int32_t seg_events;      /* longest time window of a segment-parallel merge, in child events */
     int32_t use_graph;       /* 1: replay the level sequence as a CUDA graph, -1: plain launches */
     int32_t level_occupancy; /* thread-per-merge kernel: 128-thread blocks per SM its register cap allows (1 = no cap .. 4) */
     int32_t cmp_level;       /* first level merged by the compacted warp-per-merge kernel (automatic:
@@ -70,7 +70,9 @@ typedef struct {
     int32_t seg_min_events;  /* from seg_level on, merges with fewer child events use the compacted kernel */
     int32_t merge_order;     /* thread-per-merge levels 3-8 run their merges longest first: 1 (default),
                                 or in x-order: -1 */
-    int32_t reserved[6];
+    int32_t seg_events_min;  /* shortest time window; a merge of E child events gets 2 sqrt(E) within
+                                [seg_events_min, seg_events] */
+    int32_t reserved[5];
 } hull3d_opts;
 
 /* Creates a plan for hulls of up to max_n points (hull3d_compute*) and for

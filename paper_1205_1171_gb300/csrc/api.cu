@@ -143,6 +143,7 @@ struct Bump {
 
 int default_seg_level(const hull3d_plan_s *p);
 int default_seg_events(const hull3d_plan_s *p);
+int default_seg_events_min(const hull3d_plan_s *p);
 int default_seg_slots(const hull3d_plan_s *p);
 
 // Lays out every buffer of the plan; with base == nullptr it only measures.
@@ -173,15 +174,16 @@ size_t layout(hull3d_plan_s *p, char *base)
     {
         int Lmax = 0;
         while ((1ll << Lmax) < N) Lmax++;
-        const int sl = default_seg_level(p), K = default_seg_events(p);
+        const int sl = default_seg_level(p), Kmin = default_seg_events_min(p);
         p->S_cap = p->M_cap = 0;
         for (int lv = sl > 2 ? sl : 2; lv <= Lmax; lv++) {
             const int64_t M = (N + (1ll << lv) - 1) >> lv;
-            const int64_t smax = ((1ll << (lv + 1)) + K - 1) / K;
+            const int64_t smax = ((1ll << (lv + 1)) + Kmin - 1) / Kmin;
             if (M * smax > p->S_cap) p->S_cap = M * smax;
             if (M > p->M_cap) p->M_cap = M;
         }
-        const int64_t ocap = 2 * K + 256;
+        // window outputs (seg_out_base): 4 per rank of the padded level plus 256 per window
+        const int64_t out_cap = 4 * (1ll << Lmax) + 256 * p->S_cap;
         // start-hull entries of one level: windows x (the two child hull sizes).
         // Points on a sphere are the worst case of the workloads: its child hulls
         // hold ~0.8 sqrt(m) points, so the top levels of a 2^20-point sphere need
@@ -194,9 +196,9 @@ size_t layout(hull3d_plan_s *p, char *base)
             sb.ins_idx = b.take<int>(N);
             sb.del_idx = b.take<int>(N);
             sb.smap = b.take<int>(N);
-            sb.oW = b.take<unsigned>(p->S_cap * ocap);
-            sb.oA = b.take<int>(p->S_cap * ocap);
-            sb.oB = b.take<int>(p->S_cap * ocap);
+            sb.oW = b.take<unsigned>(out_cap);
+            sb.oA = b.take<int>(out_cap);
+            sb.oB = b.take<int>(out_cap);
             sb.ocnt = b.take<int>(p->S_cap);
             sb.bridge0 = b.take<int2>(p->M_cap);
             sb.nofit = b.take<int>(p->M_cap);
@@ -273,6 +275,12 @@ const LevelOrder *level_order(const hull3d_plan_s *p, int level, const LevelOrde
     return (p->opts.merge_order >= 0 && level >= 3 && level <= 8) ? ord : nullptr;
 }
 int default_seg_events(const hull3d_plan_s *p) { return p->opts.seg_events > 0 ? p->opts.seg_events : 512; }
+int default_seg_events_min(const hull3d_plan_s *p)
+{
+    const int K = default_seg_events(p);
+    const int k = p->opts.seg_events_min > 0 ? p->opts.seg_events_min : 128;
+    return k < K ? k : K;
+}
 int default_seg_slots(const hull3d_plan_s *p) { return p->opts.seg_slots > 0 ? p->opts.seg_slots : 1536; }
 
 // Records a phase-boundary event when profiling (one per boundary per call).
@@ -350,7 +358,8 @@ int enqueue_hull(hull3d_plan_s *p, const int32_t *d_xyz, int64_t n, int32_t *d_f
                                          level_order(p, level, &ord));
             }
             launch_seg_level(pts, n, level, p->pass, p->seg, p->pk0, p->pv0, p->pk1, p->pv1, p->npairs, p->overflow,
-                             p->pair_cap, p->S_cap, p->M_cap, default_seg_events(p), default_seg_slots(p), min_ev, p->ss,
+                             p->pair_cap, p->S_cap, p->M_cap, default_seg_events(p), default_seg_events_min(p),
+                             default_seg_slots(p), min_ev, p->ss,
                              status, st, &launches);
         } else {
             if (level >= default_cmp_level(p, L)) {
@@ -451,7 +460,8 @@ int hull3d_plan(hull3d_plan_t *out, int64_t max_n, int64_t max_clouds, const hul
     p->max_clouds = max_clouds;
     if (opts) p->opts = *opts;
     if (p->opts.fused_levels < 0 || p->opts.fused_levels > 10 || p->opts.cmp_slots < 0 || p->opts.cmp_slots > 4096 ||
-        p->opts.seg_slots < 0 || p->opts.seg_slots > 6144 || p->opts.seg_events < 0 || p->opts.seg_events > 4096) {
+        p->opts.seg_slots < 0 || p->opts.seg_slots > 6144 || p->opts.seg_events < 0 || p->opts.seg_events > 4096 ||
+        p->opts.seg_events_min < 0) {
         delete p;
         return HULL3D_ERR_INVALID_ARG;
     }
@@ -505,6 +515,7 @@ int hull3d_plan_opts(hull3d_plan_t p, hull3d_opts *out)
     out->cmp_slots = default_cmp_slots(p);
     out->seg_level = default_seg_level(p);
     out->seg_events = default_seg_events(p);
+    out->seg_events_min = default_seg_events_min(p);
     out->seg_slots = default_seg_slots(p);
     out->seg_min_events = default_seg_min_events(p);
     out->merge_order = p->opts.merge_order < 0 ? -1 : 1;

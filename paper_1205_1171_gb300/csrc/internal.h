@@ -77,12 +77,12 @@ void launch_level_cmp(const Points &pts, int64_t n, int level, PassBufs *passes,
 void launch_passthrough(int64_t n, int level, int64_t lo, PassBufs *passes, int32_t *status, cudaStream_t st);
 
 struct SegBufs;
-// One level merged time-segment-parallel (K child events per window, slot
-// tables of scap points); pairs/pair_vals and their alternates hold pair_cap
-// sort items.
+// One level merged time-segment-parallel (windows of Kmin .. K child events,
+// see seg_window_len; slot tables of scap points); pairs/pair_vals and their
+// alternates hold pair_cap sort items.
 void launch_seg_level(const Points &pts, int64_t n, int level, PassBufs *passes, SegBufs *sbufs, uint64_t *pairs,
                       uint32_t *pair_vals, uint64_t *pairs_alt, uint32_t *vals_alt, unsigned long long *npairs,
-                      int *overflow, int64_t pair_cap, int64_t S_cap, int64_t M_cap, int K, int scap,
+                      int *overflow, int64_t pair_cap, int64_t S_cap, int64_t M_cap, int K, int Kmin, int scap,
                       int min_events, const SortScratch &ss, int32_t *status, cudaStream_t st, int64_t *launches);
 
 // Faces of the root movies of both passes (level L = ceil(log2 n) in buffer L & 1):

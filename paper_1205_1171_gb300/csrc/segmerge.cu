@@ -42,7 +42,7 @@ __global__ void k_seg_bounds(SegArgs a)
     const int src = (G.level - 1) & 1;
     const int nl = pb.cnt[src][lo], nr = pb.cnt[src][mid];
     // small merges are done by the compacted kernel: no windows
-    const int S = (nl + nr > G.min_events) ? seg_count(nl, nr, G.K, G.smax) : 0;
+    const int S = (nl + nr > G.min_events) ? seg_count(nl, nr, seg_window_len(nl + nr, G.K, G.Kmin), G.smax) : 0;
     if (s == 0) {
         sb.nseg[m] = S;
         sb.nofit[m] = 0;
@@ -366,9 +366,11 @@ __device__ void seg_window(const SegArgs &a, int pass, int64_t g, int retry, int
         bridge_walk_warp(cp, 0, aL + aR - 1, u, v, s > 0 ? &at : (const Tri *)nullptr, upper);
         if (s == 0 && tid == 0) sb.bridge0[m] = make_int2(sRK[u], sRK[v]);
         SegIn L{ sIn }, R{ sIn + wl };
-        SegOut out{ sb.oW + g * G.ocap, sb.oA + g * G.ocap, sb.oB + g * G.ocap, sRK };
+        const int64_t ob = seg_out_base(G.level, G.smax, m, s, b0.x + b0.y);
+        SegOut out{ sb.oW + ob, sb.oA + ob, sb.oB + ob, sRK };
         int err = 0;
-        const int k = kinetic_forward_warp(cp, lk, u, v, at, s > 0, L, wl, R, wr, out, G.ocap, upper, s + 1 < S, &err);
+        const int k = kinetic_forward_warp(cp, lk, u, v, at, s > 0, L, wl, R, wr, out, 2 * (wl + wr) + 256, upper,
+                                           s + 1 < S, &err);
         if (tid == 0) {
             sb.ocnt[g] = k;
             if (err) s_bad = 1;
@@ -425,11 +427,13 @@ __device__ void seg_concat_one(const SegArgs &a, int pass, int64_t m)
         const int chunk = min(CAT_THREADS, S - s0);
         for (int t = 0; t < chunk; t++) {
             const int64_t g = m * G.smax + s0 + t;
+            const int2 bd = sb.bound[g];
+            const int64_t ob = seg_out_base(G.level, G.smax, m, s0 + t, bd.x + bd.y);
             const int off = base + s_off[t];
             const int cnt = s_off[t + 1] - s_off[t];
             for (int e = threadIdx.x; e < cnt; e += CAT_THREADS) {
-                const unsigned w = sb.oW[g * G.ocap + e];
-                const int aa = sb.oA[g * G.ocap + e], bb = sb.oB[g * G.ocap + e];
+                const unsigned w = sb.oW[ob + e];
+                const int aa = sb.oA[ob + e], bb = sb.oB[ob + e];
                 W[off + e] = w;
                 A[off + e] = aa;
                 B[off + e] = bb;
@@ -487,7 +491,7 @@ size_t seg_smem_bytes(int scap, int K) { return (size_t)scap * (sizeof(int4) + s
 
 void launch_seg_level(const Points &pts, int64_t n, int level, PassBufs *passes, SegBufs *sbufs, uint64_t *pairs,
                       uint32_t *pair_vals, uint64_t *pairs_alt, uint32_t *vals_alt, unsigned long long *npairs,
-                      int *overflow, int64_t pair_cap, int64_t S_cap, int64_t M_cap, int K, int scap,
+                      int *overflow, int64_t pair_cap, int64_t S_cap, int64_t M_cap, int K, int Kmin, int scap,
                       int min_events, const SortScratch &ss, int32_t *status, cudaStream_t st, int64_t *launches)
 {
     SegArgs a;
@@ -495,9 +499,9 @@ void launch_seg_level(const Points &pts, int64_t n, int level, PassBufs *passes,
     a.geo.n = n;
     a.geo.level = level;
     a.geo.K = K;
-    a.geo.smax = (int)(((1ll << (level + 1)) + K - 1) / K);
+    a.geo.Kmin = Kmin;
+    a.geo.smax = (int)(((1ll << (level + 1)) + Kmin - 1) / Kmin);
     a.geo.scap = scap;
-    a.geo.ocap = 2 * K + 256;
     a.geo.pair_cap = pair_cap;
     a.geo.min_events = min_events;
     a.pb[0] = passes[0];

@@ -50,11 +50,11 @@ class Hull3DError(RuntimeError):
 
 
 OPT_NAMES = ("fused_levels", "seg_level", "seg_events", "use_graph", "level_occupancy", "cmp_level", "cmp_slots",
-             "seg_slots", "seg_min_events", "merge_order")
+             "seg_slots", "seg_min_events", "merge_order", "seg_events_min")
 
 
 class Opts(ctypes.Structure):
-    _fields_ = [(k, ctypes.c_int32) for k in OPT_NAMES] + [("reserved", ctypes.c_int32 * 6)]
+    _fields_ = [(k, ctypes.c_int32) for k in OPT_NAMES] + [("reserved", ctypes.c_int32 * 5)]
 
 
 def load():

@@ -79,12 +79,15 @@ def test_upper_level_kernels_agree(H, cmp_level, cmp_slots):
 
 
 @pytest.mark.parametrize("seg_level,seg_events,seg_slots,seg_min", [(2, 4, 64, 1), (3, 16, 256, 1), (6, 64, 2048, 1),
-                                                                    (9, 512, 2048, 1), (4, 32, 40, 1), (3, 16, 256, 64)])
+                                                                    (9, 512, 2048, 1), (4, 32, 40, 1), (3, 16, 256, 64),
+                                                                    (3, 256, 2048, 1)])
 def test_segment_parallel_levels_agree(H, seg_level, seg_events, seg_slots, seg_min):
     """Time-segment-parallel top levels (many windows per merge; tiny slot tables
     force the retry table and the serial fallback; seg_min mixes in the
     compacted kernel for small merges) give the oracle's faces."""
-    p = H.Hull3D(1 << 15, seg_level=seg_level, seg_events=seg_events, seg_slots=seg_slots, seg_min_events=seg_min)
+    # seg_events_min = 4: windows grow with the merge, 2 sqrt(E) within [4, seg_events]
+    p = H.Hull3D(1 << 15, seg_level=seg_level, seg_events=seg_events, seg_slots=seg_slots, seg_min_events=seg_min,
+                 seg_events_min=4)
     try:
         for dist in inputs.DISTS:
             for n in (3, 5, 77, 1000, 1 << 15):
