@@ -247,25 +247,33 @@ __device__ int kinetic_forward_sm(const PT &pt, LK &lk, int &u, int &v, const EI
         const int2 l0 = e0 >= 0 ? lk.get(e0) : make_int2(NIL, NIL);
         const int2 l1 = e1 >= 0 ? lk.get(e1) : make_int2(NIL, NIL);
         const int2 lu = lk.get(u), lv = lk.get(v);
-        // refresh the candidates whose triple changed (as in kinetic_forward)
-#pragma unroll 1
+        // refresh the candidates whose triple changed (as in kinetic_forward).
+        // Each lane first collects its changed candidates in a mask and then
+        // rebuilds only those: the threads of a warp, each on its own merge,
+        // change different candidates, and a loop over the six fixed slots
+        // would make the warp rebuild every slot some lane needs.
+        auto trip = [&](int l, int &tp, int &tq, int &tr) {
+            tp = l == 0 ? l0.x : l == 1 ? l1.x : l == 3 ? lu.x : u;
+            tq = l == 0 ? e0 : l == 1 ? e1 : l == 2 ? lu.y : l == 3 ? u : l == 4 ? lv.x : v;
+            tr = l == 0 ? l0.y : l == 1 ? l1.y : l == 5 ? lv.y : v;
+        };
+        unsigned chg = 0;
+#pragma unroll
         for (int l = 0; l < 6; l++) {
             int tp, tq, tr;
-            switch (l) {
-            case 0: tp = l0.x; tq = e0; tr = l0.y; break;
-            case 1: tp = l1.x; tq = e1; tr = l1.y; break;
-            case 2: tp = u; tq = lu.y; tr = v; break;
-            case 3: tp = lu.x; tq = u; tr = v; break;
-            case 4: tp = u; tq = lv.x; tr = v; break;
-            default: tp = u; tq = v; tr = lv.y; break;
-            }
-            if (tp != c.fi(0, l) || tq != c.fi(1, l) || tr != c.fi(2, l)) {
-                Tri t;
-                tri_make(pt, t, tp, tq, tr);
-                c.set(l, t);
-                bool ok = t.s != 0 && (!have_old || tri_cmp(pt, t, old, upper) > 0);
-                valid = ok ? (valid | (1u << l)) : (valid & ~(1u << l));
-            }
+            trip(l, tp, tq, tr);
+            if (tp != c.fi(0, l) || tq != c.fi(1, l) || tr != c.fi(2, l)) chg |= 1u << l;
+        }
+        while (chg) {
+            const int l = __ffs(chg) - 1;
+            chg &= chg - 1;
+            int tp, tq, tr;
+            trip(l, tp, tq, tr);
+            Tri t;
+            tri_make(pt, t, tp, tq, tr);
+            c.set(l, t);
+            bool ok = t.s != 0 && (!have_old || tri_cmp(pt, t, old, upper) > 0);
+            valid = ok ? (valid | (1u << l)) : (valid & ~(1u << l));
         }
         int best = -1;
         Tri t;
