@@ -67,7 +67,8 @@ typedef struct {
                                 log2 n - 11 within [6, 13] for a hull of n points) */
     int32_t cmp_slots;       /* its shared-memory table size in points (<= 4096) */
     int32_t seg_slots;       /* shared-memory table size of one time window in points (<= 6144) */
-    int32_t seg_min_events;  /* from seg_level on, merges with fewer child events use the compacted kernel */
+    int32_t seg_min_events;  /* from seg_level on, merges with fewer child events use the compacted kernel
+                                (automatic: 128 on levels with at most 128 merges per pass, else 512) */
     int32_t merge_order;     /* thread-per-merge levels 3-8 run their merges longest first: 1 (default),
                                 or in x-order: -1 */
     int32_t seg_events_min;  /* shortest time window; a merge of E child events gets 2 sqrt(E) within

@@ -265,6 +265,17 @@ int default_seg_min_events(const hull3d_plan_s *p)
 {
     return p->opts.seg_min_events > 0 ? p->opts.seg_min_events : 512;
 }
+// The threshold at one level of a hull of n points: where a level has few
+// merges (at most 128 per pass), a merge's serial event chain is the level's
+// critical path, so merges above 128 child events are cut into windows too
+// (2^24 cube and Gaussian: the top levels 1.2 -> 0.6 ms each; at 256 merges per
+// pass the warp kernel is still faster).
+int seg_min_events_at(const hull3d_plan_s *p, int64_t n, int level)
+{
+    if (p->opts.seg_min_events > 0) return p->opts.seg_min_events;
+    const int64_t merges = n >> level;
+    return merges <= 128 ? 128 : 512;
+}
 // Thread-per-merge levels 3-8 run their merges longest first (measured on the
 // 2^24 cube and clipped Gaussian: 3% per hull).  Level 2's merges of
 // event-free pairs are all alike, and from level 9 on there are too few merges
@@ -348,7 +359,7 @@ int enqueue_hull(hull3d_plan_s *p, const int32_t *d_xyz, int64_t n, int32_t *d_f
         if (p->profile) { int r_ = mark(p, st, &lv0); if (r_) return r_; }
         if (seg) {
             // small merges on this level's usual kernel, large ones in time windows
-            const int min_ev = default_seg_min_events(p);
+            const int min_ev = seg_min_events_at(p, n, level);
             if (level >= default_cmp_level(p, L)) {
                 launch_level_cmp(pts, n, level, p->pass, 2, status, st, default_cmp_slots(p), min_ev);
                 launches++;
