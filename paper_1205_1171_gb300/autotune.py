@@ -31,13 +31,15 @@ def bucket(n: int) -> int:
 
 
 def candidates(n: int) -> list[dict]:
-    """The search space for hulls of about n points (levels above log2 n do nothing)."""
+    """The search space for hulls of about n points (levels above log2 n do nothing).
+    0 keeps the library's automatic choice: for cmp_level the size rule, for
+    seg_min_events the per-level rule, for level_occupancy the per-level caps."""
     L = bucket(n)
-    cmp_levels = sorted({min(L + 1, c) for c in (9, 11, 13, 15)})
+    cmp_levels = sorted({0} | {min(L + 1, c) for c in (max(6, L - 12), max(6, L - 10), 13)})
     seg_levels = sorted({min(L + 1, s) for s in (8, 10, 12, 64)})
     out = []
-    for cl, sl, K, smin, occ in itertools.product(cmp_levels, seg_levels, (256, 512, 1024), (256, 512, 2048), (1, 4)):
-        if sl > L and (K != 512 or smin != 512):
+    for cl, sl, K, smin, occ in itertools.product(cmp_levels, seg_levels, (256, 512, 1024), (0, 256, 512), (0, 4)):
+        if sl > L and (K != 512 or smin != 0):
             continue  # windows never used: one representative
         out.append(dict(cmp_level=cl, seg_level=sl, seg_events=K, seg_min_events=smin, level_occupancy=occ))
     return out

@@ -11,7 +11,9 @@ def test_candidates_cover_the_knobs_and_are_unique():
     assert len(c) == len({tuple(sorted(k.items())) for k in c})
     for k in c:
         assert set(k) == set(autotune.KNOBS)
-    assert {k["level_occupancy"] for k in c} == {1, 4}
+    # 0 = the library's automatic choice, always among the candidates
+    assert {k["level_occupancy"] for k in c} == {0, 4}
+    assert 0 in {k["cmp_level"] for k in c} and 0 in {k["seg_min_events"] for k in c}
     assert {k["seg_events"] for k in c} >= {256, 512, 1024}
     small = autotune.candidates(1000)
     assert all(k["cmp_level"] <= autotune.bucket(1000) + 1 for k in small)
