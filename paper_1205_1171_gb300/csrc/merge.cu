@@ -453,32 +453,46 @@ __global__ void k_face_keys(Points pts, int64_t n, int level, PassBufs p0, PassB
 {
     const int buf = level & 1;
     const int kl = p0.cnt[buf][0], ku = p1.cnt[buf][0];
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     // a closed triangulated surface on at most n vertices has at most 2n - 4 faces
     const bool bad = (int64_t)kl + ku > 2 * n - 4;
-    if (e == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && blockIdx.y == 0) {
         if (bad) set_status2(status, HULL3D_ERR_INTERNAL);
         *d_nfaces = (*status || bad) ? 0 : (int64_t)kl + ku;
     }
     if (*status || bad) return;
     const bool upper = blockIdx.y != 0;
-    if (e >= (upper ? ku : kl)) return;
     const unsigned *W_ = upper ? p1.W[buf] : p0.W[buf];
     const int *A_ = upper ? p1.A[buf] : p0.A[buf], *B_ = upper ? p1.B[buf] : p0.B[buf];
-    int w = (int)(W_[e] & RANK_MASK), a = A_[e], b = B_[e];
+    const int cnt = upper ? ku : kl;
     GPts gp{ pts.P };
-    P3 A = gp.get(a), W = gp.get(w), Bp = gp.get(b);
-    // lower faces are oriented with the normal (w - a) x (b - a) pointing down
-    // (Y~ < 0), upper faces with it pointing up
-    bool up = turn_sign(A, W, Bp) > 0;
-    int f0 = A.id, f1, f2;
-    if (up == upper) { f1 = W.id; f2 = Bp.id; } else { f1 = Bp.id; f2 = W.id; }
-    // rotate min-first
-    if (f1 < f0 && f1 < f2) { int t = f0; f0 = f1; f1 = f2; f2 = t; }
-    else if (f2 < f0 && f2 < f1) { int t = f2; f2 = f1; f1 = f0; f0 = t; }
-    int64_t o = upper ? kl + e : e;
-    keys[o] = ((uint64_t)f0 << fbits) | (uint64_t)f1;
-    vals[o] = (uint32_t)f2;
+    // the face count is known on the device only: a grid sized to the GPU strides over it
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
+        int w = (int)(W_[e] & RANK_MASK), a = A_[e], b = B_[e];
+        P3 A = gp.get(a), W = gp.get(w), Bp = gp.get(b);
+        // lower faces are oriented with the normal (w - a) x (b - a) pointing down
+        // (Y~ < 0), upper faces with it pointing up
+        bool up = turn_sign(A, W, Bp) > 0;
+        int f0 = A.id, f1, f2;
+        if (up == upper) { f1 = W.id; f2 = Bp.id; } else { f1 = Bp.id; f2 = W.id; }
+        // rotate min-first
+        if (f1 < f0 && f1 < f2) { int t = f0; f0 = f1; f1 = f2; f2 = t; }
+        else if (f2 < f0 && f2 < f1) { int t = f2; f2 = f1; f1 = f0; f0 = t; }
+        int64_t o = upper ? kl + e : e;
+        keys[o] = ((uint64_t)f0 << fbits) | (uint64_t)f1;
+        vals[o] = (uint32_t)f2;
+    }
+}
+
+static int face_grid()
+{
+    static int g = 0;
+    if (!g) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        g = sms > 0 ? 4 * sms : 512;
+    }
+    return g;
 }
 
 void launch_face_keys(const Points &pts, int64_t n, int level, PassBufs *passes, uint64_t *keys, uint32_t *vals,
@@ -486,26 +500,29 @@ void launch_face_keys(const Points &pts, int64_t n, int level, PassBufs *passes,
 {
     int fbits = 1;
     while ((1ll << fbits) < n) fbits++;
-    int64_t cap = 2 * n;
-    dim3 g((unsigned)((cap + 255) / 256), 2);
-    k_face_keys<<<g, 256, 0, st>>>(pts, n, level, passes[0], passes[1], fbits, keys, vals, d_nfaces, status);
+    const int64_t need = (n + 255) / 256;  // at most n faces per pass
+    const unsigned gx = (unsigned)(need < face_grid() ? need : face_grid());
+    k_face_keys<<<dim3(gx, 2), 256, 0, st>>>(pts, n, level, passes[0], passes[1], fbits, keys, vals, d_nfaces, status);
 }
 
 __global__ void k_face_out(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals, int fbits,
                            const int64_t *d_nfaces, int32_t *__restrict__ faces)
 {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= *d_nfaces) return;
-    uint64_t k = keys[i];
-    faces[3 * i] = (int32_t)(k >> fbits);
-    faces[3 * i + 1] = (int32_t)(k & ((1ull << fbits) - 1));
-    faces[3 * i + 2] = (int32_t)vals[i];
+    const int64_t nf = *d_nfaces;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nf; i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t k = keys[i];
+        faces[3 * i] = (int32_t)(k >> fbits);
+        faces[3 * i + 1] = (int32_t)(k & ((1ull << fbits) - 1));
+        faces[3 * i + 2] = (int32_t)vals[i];
+    }
 }
 
 void launch_face_out(const uint64_t *keys, const uint32_t *vals, int64_t cap, int fbits, const int64_t *d_nfaces,
                           int32_t *faces, cudaStream_t st)
 {
-    k_face_out<<<(unsigned)((cap + 255) / 256), 256, 0, st>>>(keys, vals, fbits, d_nfaces, faces);
+    const int64_t need = (cap + 255) / 256;
+    const unsigned g = (unsigned)(need < face_grid() ? need : face_grid());
+    k_face_out<<<g > 0 ? g : 1, 256, 0, st>>>(keys, vals, fbits, d_nfaces, faces);
 }
 
 // Shared-memory limits of the kernels that need more than the default; set

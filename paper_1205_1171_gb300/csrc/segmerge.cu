@@ -89,21 +89,46 @@ __device__ __forceinline__ bool seg_locate(const SegGeom &G, const PassBufs &pb,
     return k < E;
 }
 
+// The child event positions of the merges that are cut into windows (the
+// work list written by k_seg_bounds): when the list is shorter than the grid,
+// several blocks share a merge; f(pass, q) gets each position q once.
+template <class F>
+__device__ __forceinline__ void for_windowed_events(const SegArgs &a, F &&f)
+{
+    const SegGeom &G = a.geo;
+    const int nm = (int)*a.nseg_merges;
+    if (nm == 0) return;
+    const int bpm = (int)gridDim.x >= nm ? (int)gridDim.x / nm : 1;  // blocks per merge
+    const int slots = (int)gridDim.x / bpm;                           // merges in flight
+    if ((int)blockIdx.x / bpm >= slots) return;
+    const int src = (G.level - 1) & 1;
+    const int64_t half = 1ll << (G.level - 1);
+    for (int idx = (int)blockIdx.x / bpm; idx < nm; idx += slots) {
+        const unsigned e = a.mlist[idx];
+        const int pass = (int)(e >> 31);
+        const int64_t m = e & 0x7fffffffu;
+        const int64_t lo = m << G.level, mid = lo + half;
+        const PassBufs &pb = a.pb[pass];
+        const int nl = pb.cnt[src][lo], nr = pb.cnt[src][mid];
+        for (int64_t t = ((int)blockIdx.x % bpm) * (int64_t)blockDim.x + threadIdx.x; t < nl + nr;
+             t += (int64_t)bpm * blockDim.x)
+            f(pass, t < nl ? 2 * lo + t : 2 * mid + (t - nl));
+    }
+}
+
 // ---- idx: every event records its index under its point --------------------
 __global__ void k_seg_idx(SegArgs a)
 {
-    if (*a.status || *a.nseg_merges == 0) return;
-    const int pass = blockIdx.y;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < 2 * a.geo.n;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        int64_t clo, plo;
-        int k, E;
-        if (!seg_locate(a.geo, a.pb[pass], q, clo, plo, k, E)) continue;
-        const unsigned w = a.pb[pass].W[(a.geo.level - 1) & 1][q];
+    if (*a.status) return;
+    const int src = (a.geo.level - 1) & 1;
+    const int64_t half = 1ll << (a.geo.level - 1);
+    for_windowed_events(a, [&](int pass, int64_t q) {
+        const unsigned w = a.pb[pass].W[src][q];
         const int rk = (int)(w & RANK_MASK);
+        const int k = (int)(q - 2 * ((q >> 1) & ~(half - 1)));  // index in the child movie
         if (w & INS_BIT) a.sb[pass].ins_idx[rk] = k;
         else a.sb[pass].del_idx[rk] = k;
-    }
+    });
 }
 
 // ---- pairs: each event point joins the start hulls of the windows it spans --
@@ -111,11 +136,8 @@ __device__ void seg_pairs_one(const SegArgs &a, int pass, int64_t q);
 
 __global__ void k_seg_pairs(SegArgs a)
 {
-    if (*a.status || *a.nseg_merges == 0) return;
-    const int pass = blockIdx.y;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < 2 * a.geo.n;
-         q += (int64_t)gridDim.x * blockDim.x)
-        seg_pairs_one(a, pass, q);
+    if (*a.status) return;
+    for_windowed_events(a, [&](int pass, int64_t q) { seg_pairs_one(a, pass, q); });
 }
 
 __device__ void seg_pairs_one(const SegArgs &a, int pass, int64_t q)
@@ -535,8 +557,8 @@ void launch_seg_level(const Points &pts, int64_t n, int level, PassBufs *passes,
     }
     int64_t fg = (2 * n + 255) / 256;
     if (fg > flat_grid) fg = flat_grid;
-    k_seg_idx<<<dim3((unsigned)fg, 2), 256, 0, st>>>(a);
-    k_seg_pairs<<<dim3((unsigned)fg, 2), 256, 0, st>>>(a);
+    k_seg_idx<<<(unsigned)fg, 256, 0, st>>>(a);
+    k_seg_pairs<<<(unsigned)fg, 256, 0, st>>>(a);
     *launches += 3;
     int key_bits = 28;
     while ((1ll << (key_bits - 28)) < 4 * S_cap) key_bits++;
