@@ -57,8 +57,10 @@ __device__ __forceinline__ void zy3(const P3 &p, const P3 &q, const P3 &r, long 
     Y = ax * by - bx * ay;
 }
 
-// sign of Y~(p, q, r): nonzero for distinct points.
-static __device__ __noinline__ int turn_slow(P3 p, P3 q, P3 r)
+// sign of Y~(p, q, r): nonzero for distinct points.  Inline: three points with
+// equal x (frequent at 2^24 points on 2^21 x-values) reach it in every bridge
+// walk over them.
+__device__ __forceinline__ int turn_slow(const P3 &p, const P3 &q, const P3 &r)
 {
     long long nx, ny, nz;
     normal3(p, q, r, nx, ny, nz);
