@@ -55,27 +55,11 @@ __device__ __forceinline__ void tri_make(const PT &pt, Tri &t, int p, int q, int
     else t.s = turn_slow(P, Q, R);
 }
 
-// The tie tiers of tri_cmp (unperturbed times equal), out of line.  The
-// triples come by value, field by field: an argument passed by reference
-// would make the caller keep its copy of the triple in local memory.
-template <class PT>
-__device__ __noinline__ int tri_cmp_tie(PT pt, int ap, int aq, int ar, int as, long long aZ, long long aY,
-                                        long long aNx, int bp, int bq, int br, int bs, long long bZ, long long bY,
-                                        long long bNx)
-{
-    if (ap == bp && aq == bq && ar == br) return 0;
-    // shear tiers: -c.z then -c.y with c = N1 x N2, N = (Nx, -Z, Y)
-    i128 cz = (i128)aZ * bNx - (i128)aNx * bZ;
-    if (cz != 0) return -sgn128(cz) * as * bs;
-    i128 cy = (i128)aY * bNx - (i128)aNx * bY;
-    if (cy != 0) return -sgn128(cy) * as * bs;
-    return time_cmp_index(pt, ap, aq, ar, bp, bq, br, as * bs);
-}
-
-// sign(t(a) - t(b)) in the pass's time direction, both finite.
-// The unperturbed value, then the cheap tie tiers inline (equal triples, the
-// shear terms -c.z and -c.y; at 2^24 points on 2^21 x-values, triples through
-// equal-x pairs tie often); only the index tiers are out of line.
+// sign(t(a) - t(b)) in the pass's time direction, both finite: the
+// unperturbed value, then the tie tiers in the perturbation's order (equal
+// triples; the shear terms -c.z and -c.y; the index tiers).  At 2^24 points on
+// 2^21 x-values, triples through equal-x pairs tie often, so every tier is
+// inline: a call would make the caller save its registers to local memory.
 template <class PT>
 __device__ __forceinline__ int tri_cmp(const PT &pt, const Tri &a, const Tri &b, bool upper)
 {
