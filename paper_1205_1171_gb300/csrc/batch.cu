@@ -20,24 +20,62 @@
 namespace hull3d {
 
 constexpr int BATCH_THREADS = 128;
-// Threads per CTA of a size class.  The 4096 class fits one cloud per SM
-// (shared memory), so it takes 256 threads: twice the warps for its
-// warp-per-merge levels (measured on the 65,536-cloud batch: that class 733 ->
-// 582 ms; 512 threads spill at the register cap they imply and are slower).
+// Threads per CTA of a size class.
 template <int NMAX>
 constexpr int batch_threads()
 {
-    return NMAX >= 4096 ? 256 : BATCH_THREADS;
+    return BATCH_THREADS;
+}
+
+// A cloud lives in shared memory in 26 bytes per point, so that two clouds of
+// the largest class share an SM: each point as its 63-bit sort key (the biased
+// x, z, y fields) and a 16-bit input index, links as two 16-bit ranks (0xffff
+// for none), movie entries as a 15-bit rank with the insertion flag in bit 15.
+constexpr unsigned short BNIL = 0xffff;
+
+struct BPts {
+    const uint64_t *K;
+    const unsigned short *ID;
+    __device__ __forceinline__ P3 get(int r) const
+    {
+        const uint64_t k = K[r];
+        const int lo = -(1 << 20);
+        return P3{ (int)((k >> 42) & 0x1fffff) + lo, (int)(k & 0x1fffff) + lo, (int)((k >> 21) & 0x1fffff) + lo,
+                   (int)ID[r], r };
+    }
+    __device__ __forceinline__ int rk(int r) const { return r; }
+};
+
+struct BLinks {
+    ushort2 *L;
+    __device__ __forceinline__ static int un(unsigned short v) { return v == BNIL ? NIL : (int)v; }
+    __device__ __forceinline__ static unsigned short pk(int v) { return v < 0 ? BNIL : (unsigned short)v; }
+    __device__ __forceinline__ int2 get(int r) const
+    {
+        const ushort2 l = L[r];
+        return make_int2(un(l.x), un(l.y));
+    }
+    __device__ __forceinline__ int prv(int r) const { return un(L[r].x); }
+    __device__ __forceinline__ int nxt(int r) const { return un(L[r].y); }
+    __device__ __forceinline__ void set(int r, int2 v) { L[r] = make_ushort2(pk(v.x), pk(v.y)); }
+    __device__ __forceinline__ void set_prv(int r, int v) { L[r].x = pk(v); }
+    __device__ __forceinline__ void set_nxt(int r, int v) { L[r].y = pk(v); }
+};
+
+__device__ __forceinline__ unsigned bw_un(unsigned short s) { return (unsigned)(s & 0x7fffu) | ((s & 0x8000u) ? INS_BIT : 0u); }
+__device__ __forceinline__ unsigned short bw_pk(unsigned w)
+{
+    return (unsigned short)((w & RANK_MASK) | ((w & INS_BIT) ? 0x8000u : 0u));
 }
 
 struct BEvIn {
-    const unsigned *W;
-    __device__ __forceinline__ unsigned w(int i) const { return W[i]; }
+    const unsigned short *W;
+    __device__ __forceinline__ unsigned w(int i) const { return bw_un(W[i]); }
 };
 struct BEvOut {
-    unsigned *W;
-    __device__ __forceinline__ void put(int k, unsigned w, int, int) { W[k] = w; }
-    __device__ __forceinline__ unsigned w(int k) const { return W[k]; }
+    unsigned short *W;
+    __device__ __forceinline__ void put(int k, unsigned w, int, int) { W[k] = bw_pk(w); }
+    __device__ __forceinline__ unsigned w(int k) const { return bw_un(W[k]); }
 };
 
 // Root merge output: each event (a, w, b) is a face; it is oriented (lower
@@ -45,16 +83,14 @@ struct BEvOut {
 // f0 << 26 | f1 << 13 | f2 (local indices below 2^13), staged as two 32-bit
 // halves in the cloud's output rows (which are only 4-byte aligned).
 struct FaceKeyOut {
-    const int4 *P;
+    BPts P;
     unsigned *keys;
     int base;
     bool upper;
     __device__ __forceinline__ void put(int k, unsigned w, int a, int b)
     {
         const int wi = (int)(w & RANK_MASK);
-        const P3 A = P3{ P[a].x, P[a].y, P[a].z, P[a].w, a };
-        const P3 W = P3{ P[wi].x, P[wi].y, P[wi].z, P[wi].w, wi };
-        const P3 B = P3{ P[b].x, P[b].y, P[b].z, P[b].w, b };
+        const P3 A = P.get(a), W = P.get(wi), B = P.get(b);
         const bool up = turn_sign(A, W, B) > 0;
         int f0 = A.id, f1, f2;
         if (up == upper) { f1 = W.id; f2 = B.id; } else { f1 = B.id; f2 = W.id; }
@@ -92,12 +128,18 @@ __device__ __forceinline__ int pow2_at_least(int x)
     return m;
 }
 
-// Shared memory per class: region A (sort keys + payload, later the movie
-// ping-pong buffers and counts, finally the face keys), points, links.
+// Shared memory per class, 26 bytes per point: the points (sort keys, sorted
+// in place with their input indices), the links, and region A with the two
+// movie buffers (2 NMAX entries each) and their counts.  After the last merge
+// the face keys are sorted over the whole of it.
 template <int NMAX>
 struct BatchSmem {
-    static constexpr int A_BYTES = (20 * NMAX > 16 * NMAX ? 20 * NMAX : 16 * NMAX);
-    static constexpr size_t bytes = (size_t)A_BYTES + sizeof(int4) * NMAX + sizeof(int2) * NMAX;
+    static constexpr size_t K_OFF = 0;                    // uint64 [NMAX]
+    static constexpr size_t ID_OFF = 8 * (size_t)NMAX;    // uint16 [NMAX]
+    static constexpr size_t LK_OFF = 10 * (size_t)NMAX;   // ushort2 [NMAX]
+    static constexpr size_t A_OFF = 14 * (size_t)NMAX;    // uint16 [2 NMAX] x 2, uint16 [NMAX] x 2
+    static constexpr size_t bytes = 26 * (size_t)NMAX;
+    static_assert(16 * NMAX <= 26 * NMAX, "face keys: at most 2 NMAX of 8 bytes");
 };
 
 // CTAs of a class that fit in an SM's 228 KB of shared memory (at most 4):
@@ -118,9 +160,10 @@ __global__ void __launch_bounds__(batch_threads<NMAX>(), batch_ctas_per_sm<NMAX>
 {
     extern __shared__ __align__(16) unsigned char bsm[];
     __shared__ int s_cloud, s_err, s_kl;
-    unsigned char *regA = bsm;
-    int4 *P = (int4 *)(bsm + BatchSmem<NMAX>::A_BYTES);
-    int2 *LK = (int2 *)(P + NMAX);
+    uint64_t *K = (uint64_t *)(bsm + BatchSmem<NMAX>::K_OFF);
+    unsigned short *ID = (unsigned short *)(bsm + BatchSmem<NMAX>::ID_OFF);
+    ushort2 *LK = (ushort2 *)(bsm + BatchSmem<NMAX>::LK_OFF);
+    unsigned char *regA = bsm + BatchSmem<NMAX>::A_OFF;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (;;) {
         if (tid == 0) s_cloud = atomicAdd(counter, 1);
@@ -136,9 +179,8 @@ __global__ void __launch_bounds__(batch_threads<NMAX>(), batch_ctas_per_sm<NMAX>
         if (tid == 0) s_err = 0;
         __syncthreads();
         // 1. keys
-        uint64_t *K = (uint64_t *)regA;
         const int m = pow2_at_least(n);
-        unsigned short *V = (unsigned short *)(K + m);
+        unsigned short *V = ID;
         for (int i = tid; i < m; i += blockDim.x) {
             if (i < n) {
                 const int x = xyz[3 * (o + i)], y = xyz[3 * (o + i) + 1], z = xyz[3 * (o + i) + 2];
@@ -153,34 +195,29 @@ __global__ void __launch_bounds__(batch_threads<NMAX>(), batch_ctas_per_sm<NMAX>
             }
         }
         __syncthreads();
-        // 2. sort, duplicates, decode
+        // 2. sort in place (the sorted keys are the points), duplicates
         bitonic_kv(K, V, m);
-        for (int i = tid; i < n; i += blockDim.x) {
+        for (int i = tid; i < n; i += blockDim.x)
             if (i > 0 && K[i - 1] == K[i]) s_err = HULL3D_ERR_DUPLICATE;
-            const uint64_t k = K[i];
-            const int lo = -(1 << 20);
-            P[i] = make_int4((int)((k >> 42) & 0x1fffff) + lo, (int)(k & 0x1fffff) + lo,
-                             (int)((k >> 21) & 0x1fffff) + lo, (int)V[i]);
-        }
         __syncthreads();
         int nf = 0;
         if (!s_err && n >= 3) {
             // 3. merge levels; region A now holds the movie buffers and counts
-            unsigned *W0 = (unsigned *)regA, *W1 = W0 + 2 * NMAX;
-            unsigned short *C0 = (unsigned short *)(W1 + 2 * NMAX), *C1 = C0 + NMAX;
+            unsigned short *W0 = (unsigned short *)regA, *W1 = W0 + 2 * NMAX;
+            unsigned short *C0 = W1 + 2 * NMAX, *C1 = C0 + NMAX;
             int L = 0;
             while ((1 << L) < n) L++;
-            SPts sp{ P, 0 };
-            SLinks lk{ LK, 0 };
+            const BPts sp{ K, ID };
+            BLinks lk{ LK };
             for (int pass = 0; pass < 2; pass++) {
                 const bool upper = pass != 0;
                 for (int i = tid; i < n; i += blockDim.x) {
-                    LK[i] = make_int2(NIL, NIL);
+                    LK[i] = make_ushort2(BNIL, BNIL);
                     C0[i] = 0;
                 }
                 __syncthreads();
                 for (int level = 1; level <= L; level++) {
-                    unsigned *Wsrc = (level & 1) ? W0 : W1, *Wdst = (level & 1) ? W1 : W0;
+                    unsigned short *Wsrc = (level & 1) ? W0 : W1, *Wdst = (level & 1) ? W1 : W0;
                     unsigned short *Csrc = (level & 1) ? C0 : C1, *Cdst = (level & 1) ? C1 : C0;
                     const int half = 1 << (level - 1);
                     const int nodes = (n + 2 * half - 1) / (2 * half);
@@ -222,7 +259,7 @@ __global__ void __launch_bounds__(batch_threads<NMAX>(), batch_ctas_per_sm<NMAX>
                             int err = 0;
                             if (root) {
                                 const int base = pass ? s_kl : 0;
-                                FaceKeyOut fo{ P, fkeys, base, upper };
+                                FaceKeyOut fo{ sp, fkeys, base, upper };
                                 // the staging rows hold 12 (2n - 4) bytes = 3n - 6 keys of 8 bytes
                                 const int room = 3 * n - 6 - base > 0 ? 3 * n - 6 - base : 0;
                                 const int k = kinetic_forward_warp(sp, lk, u, v, none, false, Lm, Csrc[llo], Rm,
@@ -251,9 +288,10 @@ __global__ void __launch_bounds__(batch_threads<NMAX>(), batch_ctas_per_sm<NMAX>
             nf = s_kl + ((L & 1) ? C1 : C0)[0];
             if (nf > 2 * n - 4) s_err = HULL3D_ERR_INTERNAL;
             __syncthreads();
-            // 5. canonical order: sort the face keys (region A) and write the faces
+            // 5. canonical order: sort the face keys (over the whole shared region,
+            // the points and links being no longer needed) and write the faces
             if (!s_err) {
-                uint64_t *FK = (uint64_t *)regA;
+                uint64_t *FK = (uint64_t *)bsm;
                 const int mf = pow2_at_least(nf);
                 for (int i = tid; i < mf; i += blockDim.x)
                     FK[i] = i < nf ? ((uint64_t)fkeys[2 * i + 1] << 32) | fkeys[2 * i] : ~0ull;
