@@ -150,23 +150,32 @@ __device__ int kinetic_forward(const PT &pt, LK &lk, int &u, int &v, Tri old, bo
         const int2 lu = lk.get(u), lv = lk.get(v);
         // refresh the candidates whose triple changed; an unchanged candidate
         // keeps its validity (it was later than the previous event, hence
-        // later than the one just taken, which had a different triple)
-#pragma unroll 1
+        // later than the one just taken, which had a different triple).  The
+        // changed ones are collected first, so that threads of a warp working
+        // on different merges rebuild only their own.
+        //   0: next event of the left child   1: next event of the right child
+        //   2: u advances to u.next           3: u retreats to u.prev
+        //   4: v retreats to v.prev           5: v advances to v.next
+        auto trip = [&](int l, int &tp, int &tq, int &tr) {
+            tp = l == 0 ? l0.x : l == 1 ? l1.x : l == 3 ? lu.x : u;
+            tq = l == 0 ? e0 : l == 1 ? e1 : l == 2 ? lu.y : l == 3 ? u : l == 4 ? lv.x : v;
+            tr = l == 0 ? l0.y : l == 1 ? l1.y : l == 5 ? lv.y : v;
+        };
+        unsigned chg = 0;
+#pragma unroll
         for (int l = 0; l < 6; l++) {
             int tp, tq, tr;
-            switch (l) {
-            case 0: tp = l0.x; tq = e0; tr = l0.y; break;  // next event of the left child
-            case 1: tp = l1.x; tq = e1; tr = l1.y; break;  // next event of the right child
-            case 2: tp = u; tq = lu.y; tr = v; break;      // u advances to u.next
-            case 3: tp = lu.x; tq = u; tr = v; break;      // u retreats to u.prev
-            case 4: tp = u; tq = lv.x; tr = v; break;      // v retreats to v.prev
-            default: tp = u; tq = v; tr = lv.y; break;     // v advances to v.next
-            }
-            if (tp != c[l].p || tq != c[l].q || tr != c[l].r) {
-                tri_make(pt, c[l], tp, tq, tr);
-                bool ok = c[l].s != 0 && (!have_old || tri_cmp(pt, c[l], old, upper) > 0);
-                valid = ok ? (valid | (1u << l)) : (valid & ~(1u << l));
-            }
+            trip(l, tp, tq, tr);
+            if (tp != c[l].p || tq != c[l].q || tr != c[l].r) chg |= 1u << l;
+        }
+        while (chg) {
+            const int l = __ffs(chg) - 1;
+            chg &= chg - 1;
+            int tp, tq, tr;
+            trip(l, tp, tq, tr);
+            tri_make(pt, c[l], tp, tq, tr);
+            bool ok = c[l].s != 0 && (!have_old || tri_cmp(pt, c[l], old, upper) > 0);
+            valid = ok ? (valid | (1u << l)) : (valid & ~(1u << l));
         }
         int best = -1;
 #pragma unroll 1
