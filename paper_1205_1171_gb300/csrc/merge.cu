@@ -47,6 +47,15 @@ void launch_level1(int64_t n, PassBufs *passes, int npass, int32_t *status, cuda
 // ---------------------------------------------------------------------------
 // The event loop's candidates live in shared memory (cand_smem_bytes of
 // dynamic shared memory) rather than in a per-thread local array.
+// Adds the events of a level to its statistics counter, one atomic per group of
+// converged threads (the merges of a level number in the millions).
+__device__ __forceinline__ void count_events(unsigned long long *lev_events, int level, int k)
+{
+    const unsigned m = __activemask();
+    const unsigned sum = __reduce_add_sync(m, (unsigned)k);
+    if ((int)(threadIdx.x & 31) == __ffs(m) - 1 && sum) atomicAdd(lev_events + level, (unsigned long long)sum);
+}
+
 // Merge order of one level: the (pass, node) entries sorted by the merge's
 // child event count, longest first.  In x-order, neighbouring merges take
 // quite different numbers of rounds and a warp runs as long as its longest
@@ -111,7 +120,7 @@ __global__ void __launch_bounds__(128, MINB) k_level(Points pts, int64_t n, int 
                                    upper, &err, cs);
     cdst[lo] = k;
     if (err) set_status2(status, HULL3D_ERR_INTERNAL);
-    atomicAdd((upper ? p1.lev_events : p0.lev_events) + level, (unsigned long long)k);
+    count_events(upper ? p1.lev_events : p0.lev_events, level, k);
 }
 
 // The last node of a level may have no right child: its movie is the child's.
