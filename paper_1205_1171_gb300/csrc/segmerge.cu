@@ -91,7 +91,9 @@ __device__ __forceinline__ bool seg_locate(const SegGeom &G, const PassBufs &pb,
 
 // The child event positions of the merges that are cut into windows (the
 // work list written by k_seg_bounds): when the list is shorter than the grid,
-// several blocks share a merge; f(pass, q) gets each position q once.
+// several blocks share a merge; f(pass, q, valid) gets each position q once
+// with valid = true (and is also called with valid = false to keep the lanes
+// of a warp together).
 template <class F>
 __device__ __forceinline__ void for_windowed_events(const SegArgs &a, F &&f)
 {
@@ -110,9 +112,12 @@ __device__ __forceinline__ void for_windowed_events(const SegArgs &a, F &&f)
         const int64_t lo = m << G.level, mid = lo + half;
         const PassBufs &pb = a.pb[pass];
         const int nl = pb.cnt[src][lo], nr = pb.cnt[src][mid];
-        for (int64_t t = ((int)blockIdx.x % bpm) * (int64_t)blockDim.x + threadIdx.x; t < nl + nr;
+        // warp-uniform trip count: every lane of a warp calls f in each round
+        // (valid = false past the end), so f may use warp collectives
+        const int64_t lane = threadIdx.x & 31;
+        for (int64_t t = ((int)blockIdx.x % bpm) * (int64_t)blockDim.x + threadIdx.x; t - lane < nl + nr;
              t += (int64_t)bpm * blockDim.x)
-            f(pass, t < nl ? 2 * lo + t : 2 * mid + (t - nl));
+            f(pass, t < nl ? 2 * lo + t : 2 * mid + (t - nl), t < nl + nr);
     }
 }
 
@@ -122,7 +127,8 @@ __global__ void k_seg_idx(SegArgs a)
     if (*a.status) return;
     const int src = (a.geo.level - 1) & 1;
     const int64_t half = 1ll << (a.geo.level - 1);
-    for_windowed_events(a, [&](int pass, int64_t q) {
+    for_windowed_events(a, [&](int pass, int64_t q, bool valid) {
+        if (!valid) return;
         const unsigned w = a.pb[pass].W[src][q];
         const int rk = (int)(w & RANK_MASK);
         const int k = (int)(q - 2 * ((q >> 1) & ~(half - 1)));  // index in the child movie
@@ -132,58 +138,83 @@ __global__ void k_seg_idx(SegArgs a)
 }
 
 // ---- pairs: each event point joins the start hulls of the windows it spans --
-__device__ void seg_pairs_one(const SegArgs &a, int pass, int64_t q);
+__device__ void seg_pairs_one(const SegArgs &a, int pass, int64_t q, bool valid);
 
 __global__ void k_seg_pairs(SegArgs a)
 {
     if (*a.status) return;
-    for_windowed_events(a, [&](int pass, int64_t q) { seg_pairs_one(a, pass, q); });
+    for_windowed_events(a, [&](int pass, int64_t q, bool valid) { seg_pairs_one(a, pass, q, valid); });
 }
 
-__device__ void seg_pairs_one(const SegArgs &a, int pass, int64_t q)
+__device__ void seg_pairs_one(const SegArgs &a, int pass, int64_t q, bool valid)
 {
+    // Called by all 32 lanes of a warp together.  Each lane finds the windows
+    // whose start hull holds its event point; the warp then reserves room for
+    // all of its entries with one atomic (a single counter serves the level).
     const SegGeom &G = a.geo;
-    int64_t clo, plo;
-    int k, E;
+    int64_t clo = 0, plo = 0;
+    int k = 0, E = 0, cnt = 0, s_first = 0, rk = 0, child = 0;
+    int64_t m = 0;
     const PassBufs &pb = a.pb[pass];
     const SegBufs &sb = a.sb[pass];
-    if (!seg_locate(G, pb, q, clo, plo, k, E)) return;
-    const unsigned *CW = pb.W[(G.level - 1) & 1] + 2 * clo;
-    const unsigned w = CW[k];
-    const int rk = (int)(w & RANK_MASK);
-    int lo_p, hi_p;  // alive after i child events iff lo_p < i <= hi_p
-    if (w & INS_BIT) {
-        lo_p = k;
-        const int dd = sb.del_idx[rk];
-        hi_p = (dd > k && dd < E && (int)(CW[dd] & RANK_MASK) == rk && !(CW[dd] & INS_BIT)) ? dd : E;
-    } else {
-        const int ii = sb.ins_idx[rk];
-        if (ii >= 0 && ii < k && (int)(CW[ii] & RANK_MASK) == rk && (CW[ii] & INS_BIT)) return;  // counted at its insert
-        lo_p = -1;
-        hi_p = k;
+    if (valid && seg_locate(G, pb, q, clo, plo, k, E)) {
+        const unsigned *CW = pb.W[(G.level - 1) & 1] + 2 * clo;
+        const unsigned w = CW[k];
+        rk = (int)(w & RANK_MASK);
+        int lo_p = 0, hi_p = -1;  // alive after i child events iff lo_p < i <= hi_p
+        bool counted = true;
+        if (w & INS_BIT) {
+            lo_p = k;
+            const int dd = sb.del_idx[rk];
+            hi_p = (dd > k && dd < E && (int)(CW[dd] & RANK_MASK) == rk && !(CW[dd] & INS_BIT)) ? dd : E;
+        } else {
+            const int ii = sb.ins_idx[rk];
+            // a point inserted before its delete is counted at its insert
+            counted = !(ii >= 0 && ii < k && (int)(CW[ii] & RANK_MASK) == rk && (CW[ii] & INS_BIT));
+            lo_p = -1;
+            hi_p = k;
+        }
+        if (counted) {
+            child = clo == plo ? 0 : 1;
+            m = plo >> G.level;
+            const int S = sb.nseg[m];
+            const int2 *bd = sb.bound + m * G.smax;
+            // windows s with lo_p < kC_s <= hi_p (kC_s is nondecreasing in s)
+            int b0 = 0, b1 = S;
+            while (b0 < b1) {
+                int c = (b0 + b1) >> 1;
+                int kc = child ? bd[c].y : bd[c].x;
+                if (kc > lo_p) b1 = c; else b0 = c + 1;
+            }
+            s_first = b0;
+            b0 = s_first; b1 = S;
+            while (b0 < b1) {
+                int c = (b0 + b1) >> 1;
+                int kc = child ? bd[c].y : bd[c].x;
+                if (kc <= hi_p) b0 = c + 1; else b1 = c;
+            }
+            cnt = b0 - s_first;
+        }
     }
-    const int child = clo == plo ? 0 : 1;
-    const int64_t m = plo >> G.level;
-    const int S = sb.nseg[m];
-    const int2 *bd = sb.bound + m * G.smax;
-    // windows s with lo_p < kC_s <= hi_p (kC_s is nondecreasing in s)
-    int b0 = 0, b1 = S;
-    while (b0 < b1) {
-        int c = (b0 + b1) >> 1;
-        int kc = child ? bd[c].y : bd[c].x;
-        if (kc > lo_p) b1 = c; else b0 = c + 1;
+    // exclusive prefix of cnt over the warp, one atomic for the warp's total
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    int incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, off);
+        if (lane >= off) incl += y;
     }
-    const int s_first = b0;
-    b0 = s_first; b1 = S;
-    while (b0 < b1) {
-        int c = (b0 + b1) >> 1;
-        int kc = child ? bd[c].y : bd[c].x;
-        if (kc <= hi_p) b0 = c + 1; else b1 = c;
+    const int total = __shfl_sync(FULL, incl, 31);
+    unsigned long long base = 0;
+    if (lane == 31 && total > 0) base = atomicAdd(a.npairs, (unsigned long long)total);
+    base = __shfl_sync(FULL, base, 31);
+    if (total == 0) return;
+    if (base + (unsigned long long)total > (unsigned long long)G.pair_cap) {
+        if (lane == 0) atomicExch(a.overflow, 1);
+        return;
     }
-    const int cnt = b0 - s_first;
-    if (cnt <= 0) return;
-    unsigned long long pos = atomicAdd(a.npairs, (unsigned long long)cnt);
-    if (pos + cnt > (unsigned long long)G.pair_cap) { atomicExch(a.overflow, 1); return; }
+    unsigned long long pos = base + (unsigned long long)(incl - cnt);
     for (int s = s_first; s < s_first + cnt; s++) a.pairs[pos++] = seg_key(pass, m * G.smax + s, child, rk, a.S_cap);
 }
 
