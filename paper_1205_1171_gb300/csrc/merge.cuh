@@ -72,7 +72,10 @@ __device__ __forceinline__ int tri_cmp(const PT &pt, const Tri &a, const Tri &b,
         if (cz != 0) s = -sgn128(cz) * a.s * b.s;
         else {
             const i128 cy = (i128)a.Y * b.Nx - (i128)a.Nx * b.Y;
-            s = cy != 0 ? -sgn128(cy) * a.s * b.s : time_cmp_index(pt, a.p, a.q, a.r, b.p, b.q, b.r, a.s * b.s);
+            if (cy != 0) s = -sgn128(cy) * a.s * b.s;
+            else if ((a.Z | a.Y | b.Z | b.Y) == 0 && a.Nx != 0 && b.Nx != 0)  // both on one x-value each
+                s = time_cmp_eqx(pt, a.p, a.q, a.r, b.p, b.q, b.r, a.Nx, b.Nx, a.s * b.s);
+            else s = time_cmp_index(pt, a.p, a.q, a.r, b.p, b.q, b.r, a.s * b.s);
         }
     }
     return upper ? -s : s;

@@ -198,4 +198,38 @@ __device__ __forceinline__ int time_cmp_index(PT pt, int a0, int a1, int a2, int
     return 0;  // unreachable for distinct sets
 }
 
+// time_cmp_index for two triples that each lie on one x-value (Z = Y = 0 and
+// Nx != 0, so dx = 0 in every w and N = (Nx, 0, 0)).  Then the gam_id
+// coefficient of D has no 1, a or b terms: its a^2 and a^3 coefficients are
+//   -(w1.dz n2x - w2.dz n1x)   and   -(w1.dy n2x - w2.dy n1x)
+// and the a^3 b, a^4 b ones repeat them negated.  The smallest id in only one
+// triple has w = 0 in the other and a nonzero (dz, dy) in its own (the other
+// two points of that triple are distinct on one x), so an unequal pair is
+// always decided in the gam tiers.  n1x, n2x are the triples' cached Nx.
+template <class PT>
+__device__ __forceinline__ int time_cmp_eqx(PT pt, int a0, int a1, int a2, int b0, int b1, int b2, long long n1x,
+                                            long long n2x, int ss)
+{
+    const P3 A[3] = { pt.get(a0), pt.get(a1), pt.get(a2) };
+    const P3 B[3] = { pt.get(b0), pt.get(b1), pt.get(b2) };
+    int prev = -1;
+    for (int t = 0; t < 6; t++) {
+        int id = 0x7fffffff;
+        for (int i = 0; i < 3; i++) {
+            if (A[i].id > prev && A[i].id < id) id = A[i].id;
+            if (B[i].id > prev && B[i].id < id) id = B[i].id;
+        }
+        if (id == 0x7fffffff) break;
+        prev = id;
+        long long w1[3], w2[3];
+        wcoef(A, id, w1);
+        wcoef(B, id, w2);
+        i128 c = (i128)w1[1] * n2x - (i128)w2[1] * n1x;
+        if (c) return -sgn128(c) * ss;
+        c = (i128)w1[2] * n2x - (i128)w2[2] * n1x;
+        if (c) return -sgn128(c) * ss;
+    }
+    return 0;  // equal point sets
+}
+
 }  // namespace hull3d
