@@ -239,13 +239,13 @@ size_t layout(hull3d_plan_s *p, char *base)
 
 // Defaults from the measured level sweeps (2^24 cube and clipped Gaussian,
 // GB300): no fused bottom kernel; the thread-per-merge kernel with 168
-// registers (3 blocks per SM) at levels 2 and 6-8, 128 registers (4 blocks)
-// at levels 3-5 and 9, and uncapped for levels 10-12.
+// registers (3 blocks per SM) at levels 6-8, 128 registers (4 blocks) at
+// levels 2-5 and 9, and uncapped for levels 10-12.
 int default_fused(const hull3d_plan_s *p) { return p->opts.fused_levels > 0 ? p->opts.fused_levels : 1; }
 int default_occupancy(const hull3d_plan_s *p, int level)
 {
     if (p->opts.level_occupancy > 0) return p->opts.level_occupancy;
-    if (level == 2 || (level >= 6 && level <= 8)) return 3;
+    if (level >= 6 && level <= 8) return 3;
     return level <= 9 ? 4 : 1;
 }
 // First level of the compacted warp-per-merge kernel for a hull of 2^L points
