@@ -49,7 +49,7 @@ def peaks():
 # from one ncu capture of the n = 2^24 cube + Gaussian step (the command and
 # the per-level figures are in profiles/), valid for the merge sources whose
 # SHA-256 is recorded with it.
-KERNEL_TRAFFIC = {"bytes_per_launch": 3305362897, "sources_sha256": "48a6d9c811dc51150ced885d22aa4111b3f282f42aaab174373334665f4aa1c3"}
+KERNEL_TRAFFIC = {"bytes_per_launch": 3308227631, "sources_sha256": "66f484c022e1784fd8d6a3c0355d07ade54c12d32080f4fcfcb2ead4375ece26"}
 TRAFFIC_SOURCES = ("paper_1205_1171_gb300/csrc/merge.cu", "paper_1205_1171_gb300/csrc/merge.cuh",
                    "paper_1205_1171_gb300/csrc/predicates.cuh")
 
@@ -64,8 +64,11 @@ def sources_sha256() -> str:
     return h.hexdigest()
 
 
-def kernel_traffic():
-    """The recorded DRAM traffic per launch, or None once the kernel changed."""
+def kernel_traffic(npts: int = 1 << 24, dists=DISTS, default_plan: bool = True):
+    """The recorded DRAM traffic per launch: None once the kernel changed, and
+    None for any other workload or plan than the one it was captured on."""
+    if not default_plan or npts != 1 << 24 or tuple(dists) != tuple(DISTS):
+        return None
     if not KERNEL_TRAFFIC or KERNEL_TRAFFIC["sources_sha256"] != sources_sha256():
         return None
     return KERNEL_TRAFFIC["bytes_per_launch"]
@@ -438,8 +441,9 @@ def main():
     achieved = k_bytes / (k_ms / 1e3) / 1e9 if k_ms > 0 else 0.0
     ab = [alg_bytes(npts, ev, plan.fused_levels_used, nf, o["seg_level"]) for ev, nf in zip(level_ev, nface)]
     alg = {k: sum(a[k] for a in ab) for k in ab[0]}  # bytes per step
+    default_plan = not (args.fused or args.occ or args.cmp_level or args.seg_level or args.seg_events)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": kernel_traffic(), "kernel": "k_level (one thread per merge)",
+                "traffic": kernel_traffic(npts, dists, default_plan), "kernel": "k_level (one thread per merge)",
                 "levels": [klev[0], klev[-1]] if klev else [], "launches_per_step": k_launches,
                 "alg_bytes_per_launch": k_bytes / max(k_launches, 1), "ms_per_launch": k_ms / max(k_launches, 1),
                 "peak_kind": peak_kind,

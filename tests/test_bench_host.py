@@ -1,0 +1,26 @@
+"""Host-side bookkeeping of bench.py (no GPU): the recorded DRAM traffic of the
+thread-per-merge kernel is reported only for the workload and sources it was
+captured on, and the algorithmic bytes follow the per-level formula."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_traffic_only_for_the_captured_workload():
+    t = bench.kernel_traffic()
+    if bench.KERNEL_TRAFFIC["sources_sha256"] == bench.sources_sha256():
+        assert t == bench.KERNEL_TRAFFIC["bytes_per_launch"]
+    else:
+        assert t is None
+    assert bench.kernel_traffic(1 << 22) is None
+    assert bench.kernel_traffic(1 << 24, ("cube",)) is None
+    assert bench.kernel_traffic(1 << 24, bench.DISTS, default_plan=False) is None
+
+
+def test_traffic_dropped_when_the_sources_change(monkeypatch):
+    monkeypatch.setitem(bench.KERNEL_TRAFFIC, "sources_sha256", "0" * 64)
+    assert bench.kernel_traffic() is None
