@@ -55,6 +55,14 @@ __device__ __forceinline__ void tri_make(const PT &pt, Tri &t, int p, int q, int
     else t.s = turn_slow(P, Q, R);
 }
 
+// Whether tri_cmp gives two triples that each lie on one x-value their own
+// index-tier comparison (time_cmp_eqx) for points of type PT.  A point type
+// opts out by specialising this; the general index tier gives the same sign.
+template <class PT>
+struct EqxTier {
+    static constexpr bool on = true;
+};
+
 // sign(t(a) - t(b)) in the pass's time direction, both finite: the
 // unperturbed value, then the tie tiers in the perturbation's order (equal
 // triples; the shear terms -c.z and -c.y; the index tiers).  At 2^24 points on
@@ -73,7 +81,7 @@ __device__ __forceinline__ int tri_cmp(const PT &pt, const Tri &a, const Tri &b,
         else {
             const i128 cy = (i128)a.Y * b.Nx - (i128)a.Nx * b.Y;
             if (cy != 0) s = -sgn128(cy) * a.s * b.s;
-            else if ((a.Z | a.Y | b.Z | b.Y) == 0 && a.Nx != 0 && b.Nx != 0)  // both on one x-value each
+            else if (EqxTier<PT>::on && (a.Z | a.Y | b.Z | b.Y) == 0 && a.Nx != 0 && b.Nx != 0)  // one x each
                 s = time_cmp_eqx(pt, a.p, a.q, a.r, b.p, b.q, b.r, a.Nx, b.Nx, a.s * b.s);
             else s = time_cmp_index(pt, a.p, a.q, a.r, b.p, b.q, b.r, a.s * b.s);
         }
