@@ -128,6 +128,16 @@ struct hull3d_plan_s {
 
 namespace {
 
+// Shared-memory limits of every kernel that needs more than the default, for
+// the current device; set before the first launch or stream capture there.
+void kernel_attributes()
+{
+    merge_kernel_attributes();
+    sort_kernel_attributes();
+    seg_kernel_attributes();
+    batch_kernel_attributes();
+}
+
 struct Bump {
     char *base;
     size_t off, cap;
@@ -476,9 +486,7 @@ int hull3d_plan(hull3d_plan_t *out, int64_t max_n, int64_t max_clouds, const hul
         return HULL3D_ERR_INVALID_ARG;
     }
     cudaGetDevice(&p->device);
-    merge_kernel_attributes();
-    seg_kernel_attributes();
-    batch_kernel_attributes();
+    kernel_attributes();
     cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
     p->pool_bytes = layout(p, nullptr);
     cudaError_t e = cudaMalloc((void **)&p->pool, p->pool_bytes);
@@ -731,6 +739,7 @@ int static_plan_for_current_device(hull3d_plan_s **out)
     std::lock_guard<std::mutex> lock(g_static_mu);
     hull3d_plan_s *p = &g_static_plan[dev];
     if (!g_static_ready[dev]) {
+        kernel_attributes();  // this path may be the process's first use of the device
         void *base = nullptr;
         CK(cudaGetSymbolAddress(&base, g_static_scratch));
         p->max_n = HULL3D_STATIC_MAX_N;

@@ -99,6 +99,7 @@ size_t fused_smem_bytes(int l1);
 
 // Kernel attributes (shared-memory limits), set once per process before any launch.
 void merge_kernel_attributes();
+void sort_kernel_attributes();
 void seg_kernel_attributes();
 void batch_kernel_attributes();
 

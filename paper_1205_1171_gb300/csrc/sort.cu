@@ -56,7 +56,8 @@ void launch_decode(const uint64_t *keys, const uint32_t *vals, int64_t n, int4 *
 // LSD radix sort, 8-bit digits, 3 kernels per pass:
 //   hist    per-tile digit histogram -> hist[digit * T + tile]
 //   rowscan per-digit exclusive scan over tiles, row totals -> rowsum[digit]
-//   scatter stable per-tile ranking (warp match + per-warp bases) and scatter
+//   scatter stable per-tile ranking (warp match + per-warp bases), the tile
+//           staged in shared memory in digit order, written out in runs
 // ---------------------------------------------------------------------------
 constexpr int RS_THREADS = 256;
 constexpr int RS_ITEMS = SORT_TILE / RS_THREADS;  // 16
@@ -134,6 +135,13 @@ __global__ void __launch_bounds__(1024) k_rs_rowscan(uint32_t *hist, int64_t T, 
     if (threadIdx.x == 1023) rowsum[blockIdx.x] = run;
 }
 
+// The tile is ranked as before (stable: warp, then item, then lane), but each
+// item first goes to its position in the tile's digit-sorted order in shared
+// memory; the tile is then written out in that order, so consecutive threads
+// write consecutive addresses of one digit's output run instead of 32 scattered
+// buckets per store.
+constexpr size_t RS_STAGE_BYTES = (size_t)SORT_TILE * (sizeof(uint64_t) + sizeof(uint32_t));
+
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *__restrict__ kin,
                                                            const uint32_t *__restrict__ vin,
                                                            uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
@@ -141,75 +149,108 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *__res
                                                            const uint32_t *__restrict__ hist, int64_t T,
                                                            const uint32_t *__restrict__ rowsum)
 {
-    __shared__ uint32_t dbase[256];
+    extern __shared__ __align__(16) unsigned char rs_stage[];
+    uint64_t *sk = (uint64_t *)rs_stage;         // [SORT_TILE] keys in tile order by digit
+    uint32_t *sv = (uint32_t *)(sk + SORT_TILE);  // [SORT_TILE] their values
+    __shared__ uint32_t gofs[256];                // output index of tile position 0 of each digit's run
     __shared__ uint32_t wh[RS_WARPS][256];
     __shared__ uint32_t ws[RS_WARPS];
     const int64_t cnt = count_of(n, d_n);
     const int64_t Tu = (cnt + SORT_TILE - 1) / SORT_TILE;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    for (int64_t tile = blockIdx.x; tile < Tu; tile += gridDim.x) {
-    const int64_t base = tile * SORT_TILE;
-
-    // digit bases: exclusive scan of the row totals, plus this tile's row prefix
-    {
-        uint32_t v = rowsum[tid];
-        uint32_t x = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) ws[w] = x;
-        __syncthreads();
-        uint32_t off = 0;
-        for (int k = 0; k < w; k++) off += ws[k];
-        dbase[tid] = off + x - v + hist[tid * T + tile];
-    }
-#pragma unroll
-    for (int k = 0; k < RS_WARPS; k++) wh[k][tid] = 0;
-    __syncthreads();
-
-    uint64_t kk[RS_ITEMS];
-    uint32_t vv[RS_ITEMS];
-    int dd[RS_ITEMS];
-    const int64_t wbase = base + w * (32 * RS_ITEMS);
-#pragma unroll
-    for (int r = 0; r < RS_ITEMS; r++) {
-        int64_t i = wbase + r * 32 + lane;
-        if (i < cnt) { kk[r] = kin[i]; vv[r] = vin[i]; dd[r] = (int)((kk[r] >> shift) & 0xff); }
-        else { kk[r] = 0; vv[r] = 0; dd[r] = 256 + lane; }
-    }
-    // per-warp digit counts
     const unsigned lt = (1u << lane) - 1u;
+    for (int64_t tile = blockIdx.x; tile < Tu; tile += gridDim.x) {
+        const int64_t base = tile * SORT_TILE;
+        const int nvalid = (int)(cnt - base < SORT_TILE ? cnt - base : SORT_TILE);
+
+        // output base of digit tid for this tile: exclusive scan of the row
+        // totals plus this tile's row prefix
+        uint32_t obase;
+        {
+            const uint32_t v = rowsum[tid];
+            uint32_t x = v;
 #pragma unroll
-    for (int r = 0; r < RS_ITEMS; r++) {
-        unsigned peers = __match_any_sync(0xffffffffu, dd[r]);
-        if (dd[r] < 256 && (peers & lt) == 0) wh[w][dd[r]] += __popc(peers);
-        __syncwarp();
-    }
-    __syncthreads();
-    {  // per-warp bases for digit tid
-        uint32_t run = dbase[tid];
-#pragma unroll
-        for (int k = 0; k < RS_WARPS; k++) {
-            uint32_t t = wh[k][tid];
-            wh[k][tid] = run;
-            run += t;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) ws[w] = x;
+            __syncthreads();
+            uint32_t off = 0;
+            for (int k = 0; k < w; k++) off += ws[k];
+            obase = off + x - v + hist[tid * T + tile];
         }
-    }
-    __syncthreads();
 #pragma unroll
-    for (int r = 0; r < RS_ITEMS; r++) {
-        unsigned peers = __match_any_sync(0xffffffffu, dd[r]);
-        uint32_t pos = 0;
-        if (dd[r] < 256) pos = wh[w][dd[r]] + __popc(peers & lt);
-        __syncwarp();
-        if (dd[r] < 256 && (peers & lt) == 0) wh[w][dd[r]] += __popc(peers);
-        __syncwarp();
-        if (dd[r] < 256) { kout[pos] = kk[r]; vout[pos] = vv[r]; }
+        for (int k = 0; k < RS_WARPS; k++) wh[k][tid] = 0;
+        __syncthreads();
+
+        uint64_t kk[RS_ITEMS];
+        uint32_t vv[RS_ITEMS];
+        int dd[RS_ITEMS];
+        const int64_t wbase = base + w * (32 * RS_ITEMS);
+#pragma unroll
+        for (int r = 0; r < RS_ITEMS; r++) {
+            const int64_t i = wbase + r * 32 + lane;
+            if (i < cnt) { kk[r] = kin[i]; vv[r] = vin[i]; dd[r] = (int)((kk[r] >> shift) & 0xff); }
+            else { kk[r] = 0; vv[r] = 0; dd[r] = 256 + lane; }
+        }
+        // per-warp digit counts
+#pragma unroll
+        for (int r = 0; r < RS_ITEMS; r++) {
+            const unsigned peers = __match_any_sync(0xffffffffu, dd[r]);
+            if (dd[r] < 256 && (peers & lt) == 0) wh[w][dd[r]] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        {  // digit tid: tile-local start of its run, and each warp's start inside it
+            uint32_t tot = 0;
+#pragma unroll
+            for (int k = 0; k < RS_WARPS; k++) tot += wh[k][tid];
+            uint32_t x = tot;  // inclusive scan of the digit totals over the block
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            __syncthreads();  // every thread has read ws (output bases) above
+            if (lane == 31) ws[w] = x;
+            __syncthreads();
+            uint32_t off = 0;
+            for (int k = 0; k < w; k++) off += ws[k];
+            uint32_t run = off + x - tot;  // exclusive: tile position of digit tid's first item
+            gofs[tid] = obase - run;       // (mod 2^32) output index = gofs[d] + tile position
+#pragma unroll
+            for (int k = 0; k < RS_WARPS; k++) {
+                const uint32_t t = wh[k][tid];
+                wh[k][tid] = run;
+                run += t;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < RS_ITEMS; r++) {
+            const unsigned peers = __match_any_sync(0xffffffffu, dd[r]);
+            uint32_t pos = 0;
+            if (dd[r] < 256) pos = wh[w][dd[r]] + __popc(peers & lt);
+            __syncwarp();
+            if (dd[r] < 256 && (peers & lt) == 0) wh[w][dd[r]] += __popc(peers);
+            __syncwarp();
+            if (dd[r] < 256) { sk[pos] = kk[r]; sv[pos] = vv[r]; }
+        }
+        __syncthreads();
+        for (int j = tid; j < nvalid; j += RS_THREADS) {
+            const uint64_t k = sk[j];
+            const uint32_t g = gofs[(int)((k >> shift) & 0xff)] + (uint32_t)j;
+            kout[g] = k;
+            vout[g] = sv[j];
+        }
+        __syncthreads();  // the stage and the tables are rewritten by the next tile
     }
-    __syncthreads();
-    }
+}
+
+void sort_kernel_attributes()
+{
+    cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_STAGE_BYTES);
 }
 
 int radix_sort_pairs(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int64_t n, const int64_t *d_n,
@@ -232,7 +273,7 @@ int radix_sort_pairs(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int
         int shift = 8 * p;
         k_rs_hist<<<G, RS_THREADS, 0, st>>>(ka, n, d_n, shift, s.hist, T);
         k_rs_rowscan<<<256, 1024, 0, st>>>(s.hist, T, d_n, n, s.rowsum);
-        k_rs_scatter<<<G, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, d_n, shift, s.hist, T, s.rowsum);
+        k_rs_scatter<<<G, RS_THREADS, RS_STAGE_BYTES, st>>>(ka, va, kb, vb, n, d_n, shift, s.hist, T, s.rowsum);
         if (launches) *launches += 3;
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
