@@ -73,3 +73,43 @@ def test_static_entry_refuses_sizes_above_its_maximum(H):
                                    torch.cuda.current_stream().cuda_stream)
     assert rc == H.ERR_TOO_LARGE
     assert b"HULL3D_STATIC_MAX_N" in lib.hull3d_strerror(rc)
+
+
+_FRESH = r"""
+import sys
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+from paper_1205_1171_gb300 import hull3d, inputs
+lib = hull3d.load()
+n = hull3d.STATIC_MAX_N
+x = torch.from_numpy(inputs.cloud_seeded("gauss", n, 11)).cuda()
+faces = torch.full((2 * n - 4, 3), -1, dtype=torch.int32, device="cuda")
+nf = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+rc = lib.hull3d_compute_static(x.data_ptr(), n, faces.data_ptr(), 2 * n - 4, nf.data_ptr(), st.data_ptr(),
+                               torch.cuda.current_stream().cuda_stream)
+torch.cuda.synchronize()
+assert rc == 0 and int(st.item()) == 0, (rc, int(st.item()))
+got = faces[: int(nf.item())].cpu().numpy()
+plan = hull3d.Hull3D(n)
+want = plan.compute(x).cpu().numpy()
+plan.close()
+assert np.array_equal(got, want)
+print("ok", got.shape[0])
+"""
+
+
+def test_static_entry_as_the_first_call_of_a_process(H, tmp_path):
+    # The kernels' shared-memory limits are per process: the static entry must
+    # set them itself when no plan was made before it.
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "fresh.py"
+    script.write_text(_FRESH)
+    out = subprocess.run([sys.executable, str(script), root], capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stdout + out.stderr
+    assert out.stdout.startswith("ok")
