@@ -62,7 +62,8 @@ typedef struct {
     int32_t seg_level;       /* first level merged time-segment-parallel (> log2 n: never) */
     int32_t seg_events;      /* longest time window of a segment-parallel merge, in child events */
     int32_t use_graph;       /* 1: replay the level sequence as a CUDA graph, -1: plain launches */
-    int32_t level_occupancy; /* thread-per-merge kernel: 128-thread blocks per SM its register cap allows (1 = no cap .. 4) */
+    int32_t level_occupancy; /* thread-per-merge kernel: 128-thread blocks per SM its register cap allows (1 = no cap .. 4;
+                                automatic: 4 at levels 2-5 and 9, 3 at levels 6-8, 1 above) */
     int32_t cmp_level;       /* first level merged by the compacted warp-per-merge kernel (automatic:
                                 log2 n - 11 within [6, 13] for a hull of n points) */
     int32_t cmp_slots;       /* its shared-memory table size in points (<= 4096) */
