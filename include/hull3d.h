@@ -66,7 +66,8 @@ typedef struct {
                                 automatic: 4 at levels 2-5 and 9, 3 at levels 6-8, 1 above) */
     int32_t cmp_level;       /* first level merged by the compacted warp-per-merge kernel (automatic:
                                 log2 n - 11 within [6, 13] for a hull of n points) */
-    int32_t cmp_slots;       /* its shared-memory table size in points (<= 4096) */
+    int32_t cmp_slots;       /* its shared-memory table size in points (<= 4096; automatic: 1024, and on
+                                time-window levels the 4 + seg_min_events points its largest merge needs) */
     int32_t seg_slots;       /* shared-memory table size of one time window in points (<= 6144) */
     int32_t seg_min_events;  /* from seg_level on, merges with fewer child events use the compacted kernel
                                 (automatic: 128 on levels with at most 128 merges per pass, else 512) */

@@ -270,6 +270,17 @@ int default_cmp_level(const hull3d_plan_s *p, int L)
     return c < 6 ? 6 : (c > 13 ? 13 : c);
 }
 int default_cmp_slots(const hull3d_plan_s *p) { return p->opts.cmp_slots > 0 ? p->opts.cmp_slots : 1024; }
+// The compacted kernel's table on a level whose merges above max_events child
+// events go to time windows: a merge it takes needs at most max_events + 4
+// slots, and a smaller table fits more blocks per SM (2^24 cube: levels 13-15
+// 25% faster with 544 slots than with 1024).
+int cmp_slots_at(const hull3d_plan_s *p, int max_events)
+{
+    const int d = default_cmp_slots(p);
+    if (p->opts.cmp_slots > 0 || max_events < 0) return d;
+    const int need = (max_events + 4 + 31) / 32 * 32;
+    return need < d ? need : d;
+}
 int default_seg_level(const hull3d_plan_s *p) { return p->opts.seg_level > 0 ? p->opts.seg_level : 10; }
 int default_seg_min_events(const hull3d_plan_s *p)
 {
@@ -371,7 +382,7 @@ int enqueue_hull(hull3d_plan_s *p, const int32_t *d_xyz, int64_t n, int32_t *d_f
             // small merges on this level's usual kernel, large ones in time windows
             const int min_ev = seg_min_events_at(p, n, level);
             if (level >= default_cmp_level(p, L)) {
-                launch_level_cmp(pts, n, level, p->pass, 2, status, st, default_cmp_slots(p), min_ev);
+                launch_level_cmp(pts, n, level, p->pass, 2, status, st, cmp_slots_at(p, min_ev), min_ev);
                 launches++;
             } else {
                 launches += launch_level(pts, n, level, p->pass, 2, status, st, default_occupancy(p, level), min_ev,
