@@ -52,6 +52,13 @@ def peaks():
 KERNEL_TRAFFIC = {"bytes_per_launch": 3308055331, "sources_sha256": "d1db39329cecbb9da57792613d72f6e9714fc1588756eb2a5f24fb3869a1ade2"}
 TRAFFIC_SOURCES = ("paper_1205_1171_gb300/csrc/merge.cu", "paper_1205_1171_gb300/csrc/merge.cuh",
                    "paper_1205_1171_gb300/csrc/predicates.cuh")
+# Warp and thread instructions per launch of the same kernel on the same step,
+# from one ncu capture (smsp__inst_executed.sum, smsp__thread_inst_executed.sum),
+# valid for the same sources.  They give the second roofline: instruction issue,
+# against 4 warp instructions per SM per cycle (one per SM sub-partition).
+KERNEL_ISSUE = {"warp_inst_per_launch": 1577019952, "thread_inst_per_launch": 19200567168,
+                "sources_sha256": "d1db39329cecbb9da57792613d72f6e9714fc1588756eb2a5f24fb3869a1ade2"}
+ISSUE_PER_SM_PER_CYCLE = 4
 
 
 def sources_sha256() -> str:
@@ -72,6 +79,25 @@ def kernel_traffic(npts: int = 1 << 24, dists=DISTS, default_plan: bool = True):
     if not KERNEL_TRAFFIC or KERNEL_TRAFFIC["sources_sha256"] != sources_sha256():
         return None
     return KERNEL_TRAFFIC["bytes_per_launch"]
+
+
+def kernel_issue(ms_per_launch: float, sms: int, sm_mhz: float, npts: int = 1 << 24, dists=DISTS,
+                 default_plan: bool = True):
+    """The instruction-issue roofline of the thread-per-merge kernel from the
+    recorded instruction counts and the live launch time, or None where the
+    counts do not apply (other workload, plan or sources)."""
+    if not default_plan or npts != 1 << 24 or tuple(dists) != tuple(DISTS):
+        return None
+    if not KERNEL_ISSUE or KERNEL_ISSUE["sources_sha256"] != sources_sha256() or ms_per_launch <= 0:
+        return None
+    w = KERNEL_ISSUE["warp_inst_per_launch"]
+    achieved = w / (ms_per_launch / 1e3) / 1e9
+    peak = ISSUE_PER_SM_PER_CYCLE * sms * sm_mhz / 1e3
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s", "frac": achieved / peak,
+            "warp_inst_per_launch": w,
+            "active_lanes_per_inst": KERNEL_ISSUE["thread_inst_per_launch"] / w,
+            "peak_basis": f"{ISSUE_PER_SM_PER_CYCLE} warp instructions per SM per cycle x {sms} SMs x "
+                          f"{sm_mhz:.0f} MHz (median SM clock of the timed region)"}
 
 
 def max_over_ranks(x: float, dist, device: str = "cuda") -> float:
@@ -450,6 +476,9 @@ def main():
                 "phase_ms_per_step": {k: v / steps for k, v in phase_ms.items()},
                 "phase_alg_bytes_per_step": alg,
                 "phase_gbs": {k: alg[k] / (phase_ms[k] / steps / 1e3) / 1e9 for k in alg if phase_ms[k] > 0}}
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sm_mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0
+    roofline["issue"] = kernel_issue(k_ms / max(k_launches, 1), sms, float(sm_mhz), npts, dists, default_plan)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",

@@ -24,3 +24,20 @@ def test_traffic_only_for_the_captured_workload():
 def test_traffic_dropped_when_the_sources_change(monkeypatch):
     monkeypatch.setitem(bench.KERNEL_TRAFFIC, "sources_sha256", "0" * 64)
     assert bench.kernel_traffic() is None
+
+
+def test_issue_roofline_from_the_recorded_counts():
+    sha_ok = bench.KERNEL_ISSUE["sources_sha256"] == bench.sources_sha256()
+    r = bench.kernel_issue(4.0, 152, 2000.0)
+    if not sha_ok:
+        assert r is None
+        return
+    w = bench.KERNEL_ISSUE["warp_inst_per_launch"]
+    assert r["bound"] == "alu" and r["unit"] == "Gwarp-inst/s"
+    assert abs(r["achieved"] - w / 4e-3 / 1e9) < 1e-6
+    assert abs(r["peak"] - 4 * 152 * 2.0) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    assert 1.0 <= r["active_lanes_per_inst"] <= 32.0
+    assert bench.kernel_issue(4.0, 152, 2000.0, 1 << 22) is None
+    assert bench.kernel_issue(4.0, 152, 2000.0, default_plan=False) is None
+    assert bench.kernel_issue(0.0, 152, 2000.0) is None
