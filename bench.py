@@ -240,9 +240,47 @@ def cpu_baseline_leg():
 
 BATCH_CLOUDS = 65536
 PLAIN_SAMPLE = 1024  # clouds timed through per-cloud plain launches
+ORACLE_BATCH_SAMPLE = 8192  # clouds of the batch hulled by the oracle on all host cores
 
 
-def batched_leg(hull3d, torch, steps: int):
+def _oracle_clouds(chunk):
+    """Pool worker: hulls each (points) array of the chunk with the oracle."""
+    import oracle
+
+    for x in chunk:
+        oracle.hull(x)
+    return len(chunk)
+
+
+def batched_cpu_baseline(xyz, off, sample: int = ORACLE_BATCH_SAMPLE, workers: int | None = None):
+    """The oracle over the first `sample` clouds of the batch, one cloud at a
+    time per worker process on every host core (clouds are independent).  The
+    pool is started with `spawn` and warmed up (oracle loaded in each worker)
+    before the timed map.  Never raises: a failure is reported as unavailable."""
+    import multiprocessing as mp
+
+    try:
+        import oracle
+
+        oracle.build()
+        workers = workers or os.cpu_count() or 1
+        sample = min(sample, len(off) - 1)
+        clouds = [np.ascontiguousarray(xyz[off[b]: off[b + 1]]) for b in range(sample)]
+        per = max(1, len(clouds) // (8 * workers))
+        chunks = [clouds[i: i + per] for i in range(0, len(clouds), per)]
+        with mp.get_context("spawn").Pool(workers) as pool:
+            pool.map_async(_oracle_clouds, [clouds[:1]] * workers, chunksize=1).get(timeout=120)
+            t0 = time.perf_counter()
+            done = sum(pool.map_async(_oracle_clouds, chunks, chunksize=1).get(timeout=240))
+            dt = time.perf_counter() - t0
+        return {"hulls_per_s": done / dt, "cores": workers, "kind": "oracle",
+                "sample": f"first {done} clouds of the batch ({int(off[done] - off[0])} points), one process per core",
+                "seconds": dt}
+    except Exception as e:  # the GPU legs stand without it
+        return {"unavailable": f"{type(e).__name__}: {e}"}
+
+
+def batched_leg(hull3d, torch, steps: int, cpu_baseline: bool = False):
     """65,536 independent clouds, sizes round(2^U(4, 12)), distribution drawn
     per cloud: one persistent launch per size class vs per-cloud plain launches."""
     from paper_1205_1171_gb300 import inputs
@@ -285,11 +323,14 @@ def batched_leg(hull3d, torch, steps: int):
     plain_ms = e0.elapsed_time(e1)
     plan.close()
     single.close()
-    return {"workload": "65,536 clouds, sizes round(2^U(4,12)) (16..4096), distribution per cloud uniform over "
-                        "cube/ball/sphere/gauss", "points": int(len(xyz)),
-            "hulls_per_s": BATCH_CLOUDS / (batch_ms / 1e3), "ms_per_batch": batch_ms, "launches_per_batch": launches,
-            "per_cloud_plain_hulls_per_s": PLAIN_SAMPLE / (plain_ms / 1e3),
-            "per_cloud_plain_sample": PLAIN_SAMPLE}
+    out = {"workload": "65,536 clouds, sizes round(2^U(4,12)) (16..4096), distribution per cloud uniform over "
+                       "cube/ball/sphere/gauss", "points": int(len(xyz)),
+           "hulls_per_s": BATCH_CLOUDS / (batch_ms / 1e3), "ms_per_batch": batch_ms, "launches_per_batch": launches,
+           "per_cloud_plain_hulls_per_s": PLAIN_SAMPLE / (plain_ms / 1e3),
+           "per_cloud_plain_sample": PLAIN_SAMPLE}
+    if cpu_baseline:
+        out["cpu_baseline"] = batched_cpu_baseline(xyz, off)
+    return out
 
 
 SERVE_RATE = 20000.0     # requests per second (Poisson)
@@ -488,7 +529,8 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline}
     if not args.no_batched:
-        b = batched_leg(hull3d, torch, max(1, args.steps // 2))
+        b = batched_leg(hull3d, torch, max(1, args.steps // 2),
+                        cpu_baseline=rank == 0 and world == 1 and not args.no_cpu_baseline)
         if dist:
             b["hulls_per_s"] = world * BATCH_CLOUDS / (max_over_ranks(b["ms_per_batch"], dist) / 1e3)
         line["batched"] = b

@@ -41,3 +41,13 @@ def test_issue_roofline_from_the_recorded_counts():
     assert bench.kernel_issue(4.0, 152, 2000.0, 1 << 22) is None
     assert bench.kernel_issue(4.0, 152, 2000.0, default_plan=False) is None
     assert bench.kernel_issue(0.0, 152, 2000.0) is None
+
+
+def test_batched_oracle_baseline_on_a_small_batch():
+    from paper_1205_1171_gb300 import inputs
+
+    xyz, off, _ = inputs.batch(96, inputs.seed_for(4))
+    r = bench.batched_cpu_baseline(xyz, off, sample=64, workers=2)
+    assert "unavailable" not in r, r
+    assert r["cores"] == 2 and r["kind"] == "oracle" and r["hulls_per_s"] > 0
+    assert r["sample"].startswith("first 64 clouds")
