@@ -1,16 +1,18 @@
 // Host compile of the device merge header, for a CPU regression test (test
-// infrastructure; no product code calls it).  The same kinetic_merge that the
-// batch kernel and the serial fallback run, and the compacted slot-table form
-// that the warp-per-merge kernel uses, hull a point set level by level exactly
-// as the device driver orders them (aligned blocks, both passes, faces from the
-// root movies); tests/test_merge_header_host.py compares the faces with the
-// oracle's.
+// infrastructure; no product code calls it).  The merges of the header hull a
+// point set level by level exactly as the device driver orders them (aligned
+// blocks, both passes, faces from the root movies):
+//   form 0: kinetic_merge, the loop the batch kernel and the serial fallback run;
+//   form 1: kinetic_merge_sm, the loop of the thread-per-merge level kernel,
+//           with its candidates in a one-thread CandSmem slice;
+// and, from cmp_level on (> 0), the compacted slot-table form of the
+// warp-per-merge kernel.  tests/test_merge_header_host.py compares the faces
+// with the oracle's.
 //
-//   int merge_header_hull(const int32_t *xyz, int64_t n, int cmp_level,
+//   int merge_header_hull(const int32_t *xyz, int64_t n, int form, int cmp_level,
 //                         int32_t *faces, int64_t *nfaces)
-// xyz: n x 3 int32 in [-2^20, 2^20); faces: room for 2n triples.  Levels at or
-// above cmp_level (> 0) go through the compacted form.  Returns 0, or
-// 2 (range), 3 (duplicate point), 10 + merge error.
+// xyz: n x 3 int32 in [-2^20, 2^20); faces: room for 2n triples.  Returns 0,
+// or 2 (range), 3 (duplicate point), 10 + merge error.
 #define __device__
 #define __forceinline__ inline
 #define __noinline__
@@ -98,7 +100,8 @@ int slot_merge(const int4 *P, std::vector<int2> &lk, const unsigned *Lw, int nl,
 
 }  // namespace
 
-extern "C" int merge_header_hull(const int32_t *xyz, int64_t n, int cmp_level, int32_t *faces, int64_t *nfaces)
+extern "C" int merge_header_hull(const int32_t *xyz, int64_t n, int form, int cmp_level, int32_t *faces,
+                                 int64_t *nfaces)
 {
     *nfaces = 0;
     const int bias = 1 << 20;
@@ -125,6 +128,9 @@ extern "C" int merge_header_hull(const int32_t *xyz, int64_t n, int cmp_level, i
     std::vector<uint64_t> fk;
     std::vector<int32_t> fv;
     GPts gp{ P.data() };
+    int cand_i[4 * 6];        // CandSmem of one thread: p, q, r, s of six candidates
+    long long cand_q[3 * 6];  // and their Z, Y, Nx
+    const CandSmem cs{ cand_i, cand_q, 1, 0 };
     for (int pass = 0; pass < 2; pass++) {
         const bool upper = pass != 0;
         std::vector<int2> lk(n, make_int2(NIL, NIL));
@@ -161,8 +167,12 @@ extern "C" int merge_header_hull(const int32_t *xyz, int64_t n, int cmp_level, i
                 } else {
                     GEvIn Lv{ W[src].data() + 2 * lo }, Rv{ W[src].data() + 2 * mid };
                     GEvOut out{ W[dst].data() + 2 * lo, A[dst].data() + 2 * lo, B[dst].data() + 2 * lo };
-                    k = kinetic_merge(gp, gl, (int)mid - 1, (int)mid, (int)mid, Lv, nl, Rv, nr, out,
-                                      (int)(2 * (hi - lo)), upper, &err);
+                    if (form == 1)
+                        k = kinetic_merge_sm(gp, gl, (int)mid - 1, (int)mid, (int)mid, Lv, nl, Rv, nr, out,
+                                             (int)(2 * (hi - lo)), upper, &err, cs);
+                    else
+                        k = kinetic_merge(gp, gl, (int)mid - 1, (int)mid, (int)mid, Lv, nl, Rv, nr, out,
+                                          (int)(2 * (hi - lo)), upper, &err);
                 }
                 if (err) return 10 + err;
                 C[dst][lo] = k;
