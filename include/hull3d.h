@@ -82,7 +82,9 @@ typedef struct {
  * batches of up to max_clouds clouds totalling up to max_n points
  * (hull3d_batch).  Allocates every scratch buffer up front on the current
  * device.  opts may be NULL.  On failure *out is NULL and the code is
- * HULL3D_ERR_INVALID_ARG or HULL3D_ERR_OOM. */
+ * HULL3D_ERR_INVALID_ARG or HULL3D_ERR_OOM.  Sec. 3: the point array P and
+ * the two event arrays A and B of 2n entries are allocated once, before the
+ * main loop; a plan holds those and every other buffer of the pipeline. */
 int hull3d_plan(hull3d_plan_t *out, int64_t max_n, int64_t max_clouds, const hull3d_opts *opts);
 
 /* Copies the plan's effective options (automatic fields resolved) into *out. */
@@ -108,18 +110,24 @@ int hull3d_compute_async(hull3d_plan_t plan, const int32_t *d_xyz, int64_t n, in
 
 /* Synchronous form of hull3d_compute_async: enqueues, waits for the stream,
  * stores the face count in *h_nfaces (host, may be NULL) and returns the
- * device-detected status. */
+ * device-detected status.  Sec. 2 and Sec. 3 as for hull3d_compute_async;
+ * the blocking face-count readback is an addition of this library. */
 int hull3d_compute(hull3d_plan_t plan, const int32_t *d_xyz, int64_t n, int32_t *d_faces, int64_t cap_faces,
                    int64_t *h_nfaces, void *stream);
 
 /* End-to-end form on HOST buffers: copies h_xyz (n x 3 int32) to the device,
  * computes, copies the faces back to h_faces (cap_faces x 3 int32) and the
  * count to *h_nfaces, then returns the status.  Uses plan-owned device
- * staging buffers; the host buffers should be pinned for full copy speed. */
+ * staging buffers; the host buffers should be pinned for full copy speed.
+ * Sec. 3: the host only uploads the points, runs every merge level on the
+ * GPU without reading anything back in between, and reads the result once. */
 int hull3d_compute_host(hull3d_plan_t plan, const int32_t *h_xyz, int64_t n, int32_t *h_faces, int64_t cap_faces,
                         int64_t *h_nfaces, void *stream);
 
 /* Enqueues the hulls of B independent clouds concatenated in d_xyz.
+ * Sec. 2 notes that the merges of a level are independent of one another;
+ * hulling many independent clouds in one call is an addition of this library
+ * (no paper counterpart).
  *   h_offsets       host int64 [B+1]: cloud b is rows [h_offsets[b], h_offsets[b+1]) of d_xyz
  *   d_faces         device int32 x 3: cloud b's faces start at row h_face_offsets[b]
  *   h_face_offsets  host int64 [B+1]: row capacity of cloud b is

@@ -100,6 +100,8 @@ class CudaBackend:
                 "st": torch.zeros(batch_clouds, dtype=torch.int32, device=dev),
                 "h_xyz": torch.empty((batch_points, 3), dtype=torch.int32).pin_memory(),
                 "h_faces": torch.empty((2 * batch_points, 3), dtype=torch.int32).pin_memory(),
+                "h_nf": torch.zeros(batch_clouds, dtype=torch.int64).pin_memory(),
+                "h_st": torch.zeros(batch_clouds, dtype=torch.int32).pin_memory(),
                 "busy": None})
         self.large_slots = []
         for _ in range(large_slots):
@@ -112,6 +114,8 @@ class CudaBackend:
                 "st": torch.zeros(1, dtype=torch.int32, device=dev),
                 "h_xyz": torch.empty((large_max, 3), dtype=torch.int32).pin_memory(),
                 "h_faces": torch.empty((2 * large_max, 3), dtype=torch.int32).pin_memory(),
+                "h_nf": torch.zeros(1, dtype=torch.int64).pin_memory(),
+                "h_st": torch.zeros(1, dtype=torch.int32).pin_memory(),
                 "busy": None})
 
     def resident_bytes(self) -> int:
@@ -130,8 +134,13 @@ class CudaBackend:
         with torch.cuda.stream(slot["stream"]):
             slot["h_xyz"][:n].numpy()[:] = req.points
             slot["xyz"][:n].copy_(slot["h_xyz"][:n], non_blocking=True)
-            slot["plan"].compute_async(slot["xyz"][:n], slot["faces"][: max(2 * n - 4, 1)], slot["nf"], slot["st"],
-                                       slot["stream"])
+            cap = max(2 * n - 4, 1)
+            slot["plan"].compute_async(slot["xyz"][:n], slot["faces"][:cap], slot["nf"], slot["st"], slot["stream"])
+            # results to pinned host memory on the same stream: completion
+            # then needs no device call from the scheduler thread
+            slot["h_nf"].copy_(slot["nf"], non_blocking=True)
+            slot["h_st"].copy_(slot["st"], non_blocking=True)
+            slot["h_faces"][:cap].copy_(slot["faces"][:cap], non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(slot["stream"])
         slot["busy"] = (ev, [req])
@@ -158,6 +167,9 @@ class CudaBackend:
             F = int(foff[-1])
             if F:
                 slot["h_faces"][:F].copy_(slot["faces"][:F], non_blocking=True)
+            B = len(reqs)
+            slot["h_nf"][:B].copy_(slot["nf"][:B], non_blocking=True)
+            slot["h_st"][:B].copy_(slot["st"][:B], non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(slot["stream"])
         slot["busy"] = (ev, reqs, foff)
@@ -169,19 +181,19 @@ class CudaBackend:
         for slot in self.large_slots:
             if slot["busy"] is not None and slot["busy"][0].query():
                 _, reqs = slot["busy"]
-                st = int(slot["st"].item())
+                st = int(slot["h_st"][0])
                 if st:
                     out.append((reqs[0], self.H.Hull3DError(st, "serve")))
                 else:
-                    nf = int(slot["nf"].item())
-                    out.append((reqs[0], slot["faces"][:nf].cpu().numpy()))
+                    nf = int(slot["h_nf"][0])
+                    out.append((reqs[0], slot["h_faces"][:nf].numpy().copy()))
                 slot["busy"] = None
         for slot in self.batch_slots:
             if slot["busy"] is not None and slot["busy"][0].query():
                 _, reqs, foff = slot["busy"]
                 B = len(reqs)
-                nf = slot["nf"][:B].cpu().numpy()
-                st = slot["st"][:B].cpu().numpy()
+                nf = slot["h_nf"][:B].numpy()
+                st = slot["h_st"][:B].numpy()
                 hf = slot["h_faces"].numpy()
                 for b, r in enumerate(reqs):
                     if st[b]:
@@ -328,11 +340,13 @@ def request_pool(count: int, seed: int, lo_exp: float = 6.0, hi_exp: float = 18.
             enumerate(zip(sizes, kinds))]
 
 
-def replay(server_submit, arrivals: np.ndarray, pool: list, rng: np.random.Generator):
-    """Submits pool clouds at the given arrival times (open loop); returns the futures."""
+def replay(server_submit, arrivals: np.ndarray, pool: list, picks):
+    """Submits pool[picks[i]] at arrival time arrivals[i] (open loop); returns
+    the futures.  picks may be a numpy Generator, which then draws them."""
     futs = []
+    if isinstance(picks, np.random.Generator):
+        picks = picks.integers(0, len(pool), size=len(arrivals))
     t0 = time.perf_counter()
-    picks = rng.integers(0, len(pool), size=len(arrivals))
     for t, k in zip(arrivals, picks):
         while True:
             dt = t0 + t - time.perf_counter()

@@ -1,7 +1,9 @@
 """The autotuner's search and cache logic (CPU), and on the GPU that tuned
-knobs never change the faces."""
+knobs never change the faces (against the default plan and the oracle)."""
 import numpy as np
 import pytest
+
+import oracle
 
 from paper_1205_1171_gb300 import autotune
 
@@ -53,8 +55,11 @@ def test_tuning_never_changes_the_faces(tmp_path):
     ref = hull3d.Hull3D(1 << 12)
     try:
         for d in inputs.DISTS:
-            x = torch.from_numpy(inputs.cloud_seeded(d, 4000, 3)).cuda()
-            assert np.array_equal(p.compute(x).cpu().numpy(), ref.compute(x).cpu().numpy())
+            pts = inputs.cloud_seeded(d, 4000, 3)
+            x = torch.from_numpy(pts).cuda()
+            got = p.compute(x).cpu().numpy()
+            assert np.array_equal(got, ref.compute(x).cpu().numpy())
+            assert np.array_equal(got, oracle.hull(pts)), d  # the tuned plan gives the oracle's faces
     finally:
         p.close()
         ref.close()

@@ -1,10 +1,11 @@
 """The serving loop: admission under a memory budget, continuous batching,
-and (on the GPU) results identical alone and in the mix."""
+and (on the GPU) results identical alone, in the mix and to the oracle."""
 import time
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_1205_1171_gb300 import inputs, serve
 
 
@@ -118,14 +119,24 @@ def test_results_identical_alone_and_in_the_mix():
                     got.append(f.result(timeout=120))
                 except Exception as e:  # noqa: BLE001
                     got.append(e)
+        # the oracle's faces of every distinct cloud (None: the oracle rejects it)
+        want_oracle = {}
+        for k in set(order.tolist()):
+            try:
+                want_oracle[k] = oracle.hull(pool[k])
+            except oracle.OracleError:
+                want_oracle[k] = None
         for k, g in zip(order, got):
             x = torch.from_numpy(pool[k]).cuda()
             try:
                 want = single.compute(x).cpu().numpy()
             except hull3d.Hull3DError as e:
                 assert isinstance(g, hull3d.Hull3DError) and g.code == e.code
+                assert want_oracle[k] is None, k  # the oracle rejects it too
                 continue
             assert np.array_equal(g, want), (k, len(pool[k]))
+            # served, alone and the definition (Sec. 2: one face per root event) agree
+            assert want_oracle[k] is not None and np.array_equal(g, want_oracle[k]), (k, len(pool[k]))
         assert srv.stats.batches >= 1 and srv.stats.large >= 1
     finally:
         single.close()

@@ -7,9 +7,9 @@ device).  hull3d_compute_static serves them: the caller passes input and
 output buffers, and the library's scratch comes from one static device array.
 
 This test calls it through the C ABI and checks that it gives exactly the
-faces of the planned entry point, on two calls in a row (the static array
-keeps the previous call's contents), and that sizes above its maximum are
-refused.  It is kept in its own file, collected last.
+faces of the planned entry point (and of the oracle), on two calls in a row
+(the static array keeps the previous call's contents), and that sizes above
+its maximum are refused.  It is kept in its own file, collected last.
 """
 import ctypes
 
@@ -49,12 +49,18 @@ def _static(H, x):
 
 
 def test_static_entry_matches_planned_entry_on_consecutive_calls(H):
+    import oracle
+
     plan = H.Hull3D(H.STATIC_MAX_N)
     try:
-        cases = [("sphere", 5000, 1), ("gauss", H.STATIC_MAX_N, 2), ("cube", 777, 3)]
+        # the sphere at the maximum size puts nearly every point on the hull:
+        # the largest movies this entry point can meet
+        cases = [("sphere", 5000, 1), ("gauss", H.STATIC_MAX_N, 2), ("cube", 777, 3), ("sphere", H.STATIC_MAX_N, 4)]
         for dist, n, seed in cases:
-            x = torch.from_numpy(inputs.cloud_seeded(dist, n, seed)).cuda()
+            pts = inputs.cloud_seeded(dist, n, seed)
+            x = torch.from_numpy(pts).cuda()
             want = plan.compute(x).cpu().numpy()
+            assert np.array_equal(want, oracle.hull(pts)), (dist, n)
             for _ in range(2):  # two calls in a row on the same shared array
                 got = _static(H, x)
                 assert got.shape == want.shape and np.array_equal(got, want), (dist, n)
