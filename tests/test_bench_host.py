@@ -47,7 +47,36 @@ def test_batched_oracle_baseline_on_a_small_batch():
     from paper_1205_1171_gb300 import inputs
 
     xyz, off, _ = inputs.batch(96, inputs.seed_for(4))
-    r = bench.batched_cpu_baseline(xyz, off, sample=64, workers=2)
+    r, digests = bench.batched_cpu_baseline(xyz, off, sample=64, workers=2)
     assert "unavailable" not in r, r
     assert r["cores"] == 2 and r["kind"] == "oracle" and r["hulls_per_s"] > 0
     assert r["sample"].startswith("first 64 clouds")
+    assert sorted(digests) == list(range(64))
+
+
+def test_batch_parity_accepts_the_oracle_faces_and_rejects_a_changed_face():
+    import numpy as np
+    import pytest
+    import torch
+
+    import oracle
+    from paper_1205_1171_gb300 import inputs
+
+    xyz, off, _ = inputs.batch(12, inputs.seed_for(4))
+    sizes = np.diff(off)
+    foff = np.zeros(len(off), np.int64)
+    foff[1:] = np.cumsum(np.where(sizes >= 3, 2 * sizes - 4, 0))
+    faces = np.full((int(foff[-1]), 3), -1, np.int32)
+    nf = np.zeros(12, np.int64)
+    digests = {}
+    for b in range(12):  # a batch output laid out as the GPU writes it, here from the oracle
+        f = oracle.hull(xyz[off[b]: off[b + 1]])
+        faces[foff[b]: foff[b] + len(f)] = f
+        nf[b] = len(f)
+        digests[b] = (len(f), bench.face_digest(f))
+    ft, nt = torch.from_numpy(faces), torch.from_numpy(nf)
+    assert bench.batch_parity(ft, nt, foff, digests) == {"clouds": 12, "bit_exact": True}
+    faces[foff[5] + 1, [1, 2]] = faces[foff[5] + 1, [2, 1]]  # one face turned inside out
+    with pytest.raises(RuntimeError, match="cloud 5"):
+        bench.batch_parity(torch.from_numpy(faces), nt, foff, digests)
+    assert bench.batch_parity(ft, nt, foff, {}) == {"clouds": 0, "bit_exact": None}
