@@ -50,6 +50,7 @@ extern "C" {
 #define HULL3D_ERR_CUDA 8          /* a CUDA runtime call failed (see hull3d_last_cuda_error) */
 #define HULL3D_ERR_INTERNAL 9      /* an internal consistency check failed */
 #define HULL3D_ERR_TOO_LARGE 10    /* n above HULL3D_STATIC_MAX_N (hull3d_compute_static only) */
+#define HULL3D_ERR_NOT_CLOSED 11   /* faces are not a closed, consistently oriented surface (hull3d_adjacency_async) */
 
 #define HULL3D_MAX_N (1 << 28)     /* largest n one plan accepts */
 
@@ -140,6 +141,33 @@ int hull3d_compute_host(hull3d_plan_t plan, const int32_t *h_xyz, int64_t n, int
 int hull3d_batch_async(hull3d_plan_t plan, const int32_t *d_xyz, const int64_t *h_offsets, int64_t B,
                        int32_t *d_faces, const int64_t *h_face_offsets, int64_t *d_nfaces, int32_t *d_status,
                        void *stream);
+
+/* Adjacency of a hull: the arrangement structure (a doubly connected edge
+ * list, in essence) that the paper names as the prerequisite for further
+ * geometric algorithms on the GPU (Sec. 5), built from a canonical face list
+ * such as hull3d_compute_async writes.
+ *   d_faces     device int32 [cap_faces x 3]: outward counter-clockwise faces,
+ *               rows [0, *d_nfaces) used, vertex indices in [0, n)
+ *   d_nfaces    device int64: the face count F (0 <= F <= cap_faces)
+ *   n           number of vertices (1 <= n <= the plan's max_n)
+ *   cap_faces   at most 2 * max_n
+ *   d_nb        device int32 [cap_faces x 3]: d_nb[3 f + k] is the face that
+ *               holds the directed edge d_faces[f][(k + 1) % 3] -> d_faces[f][k]
+ *               (the face across edge k of f)
+ *   d_star_off  device int64 [n + 1], d_star device int32 [3 cap_faces]: the
+ *               faces around vertex v are d_star[d_star_off[v] ..
+ *               d_star_off[v + 1]), counter-clockwise seen from outside,
+ *               starting from the smallest face index; a vertex on no face
+ *               (an interior point) has none
+ *   d_status    device int32: 0, or HULL3D_ERR_NOT_CLOSED when an edge has no
+ *               opposite, is held twice, or the faces around a vertex do not
+ *               form one cycle; HULL3D_ERR_INVALID_ARG when F > cap_faces
+ * Stream-ordered; uses the plan's scratch (serialise it with the plan's
+ * other calls on one stream).  Host-detected argument errors are returned
+ * before anything is enqueued. */
+int hull3d_adjacency_async(hull3d_plan_t plan, const int32_t *d_faces, const int64_t *d_nfaces, int64_t cap_faces,
+                           int64_t n, int32_t *d_nb, int64_t *d_star_off, int32_t *d_star, int32_t *d_status,
+                           void *stream);
 
 /* Allocation-free form of hull3d_compute_async, for hulls of at most
  * HULL3D_STATIC_MAX_N points.  The paper has no counterpart: this is a

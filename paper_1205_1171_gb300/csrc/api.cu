@@ -247,6 +247,25 @@ size_t layout(hull3d_plan_s *p, char *base)
     return b.off;
 }
 
+// The adjacency kernels' scratch, laid over the start of the plan's pool (the
+// hull's buffers are free once its faces are written): keys and edge ids for
+// 3 F <= 6 max_n directed edges, twice, and their sort histograms.  With
+// base == nullptr it only measures.
+size_t adj_layout(const hull3d_plan_s *p, char *base, AdjScratch *s)
+{
+    const int64_t E = 6 * p->max_n;
+    Bump b{ base, 0, 0 };
+    s->k0 = b.take<uint64_t>(E);
+    s->k1 = b.take<uint64_t>(E);
+    s->v0 = b.take<uint32_t>(E);
+    s->v1 = b.take<uint32_t>(E);
+    s->ss.max_tiles = (E + SORT_TILE - 1) / SORT_TILE;
+    s->ss.hist = b.take<uint32_t>(256 * s->ss.max_tiles);
+    s->ss.rowsum = b.take<uint32_t>(256);
+    s->n3 = b.take<int64_t>(1);
+    return b.off;
+}
+
 // Defaults from the measured level sweeps (2^24 cube and clipped Gaussian,
 // GB300): no fused bottom kernel; the thread-per-merge kernel with 168
 // registers (3 blocks per SM) at levels 6-8, 128 registers (4 blocks) at
@@ -366,19 +385,27 @@ int enqueue_hull(hull3d_plan_s *p, const int32_t *d_xyz, int64_t n, int32_t *d_f
     int l1 = default_fused(p);
     if (l1 > L) l1 = L;
     if (l1 > 10) l1 = 10;
-    if (l1 <= 1) launch_level1(n, p->pass, 2, status, st);  // pairs need no merge
-    else launch_fused(pts, n, 0, l1, p->pass, 2, status, st);
-    launches++;
+    if (l1 > 1) {  // otherwise the pairs of level 1 are linked by the level-2 kernel
+        launch_fused(pts, n, 0, l1, p->pass, 2, status, st);
+        launches++;
+    }
     STEP("fused levels");
     MARK(2);
     bool seg_marked = false;
     const LevelOrder ord{ p->k0, p->k1, p->v0, p->v1, p->ss };
+    // parent movies keep their event neighbours from the level below the
+    // first time-window level (whose kernels read them) and at the root
+    const int ab_level = p->S_cap ? std::min(default_seg_level(p) - 1, L) : L;
     for (int level = l1 + 1; level <= L; level++) {
-        const bool seg = level >= default_seg_level(p) && p->S_cap;
+        // level 2 merges event-free pairs: its own kernel, never time windows
+        const bool seg = level >= default_seg_level(p) && p->S_cap && level > 2;
         if (seg && !seg_marked) { MARK(3); seg_marked = true; }
         int lv0 = -1, lv1 = -1;
         if (p->profile) { int r_ = mark(p, st, &lv0); if (r_) return r_; }
-        if (seg) {
+        if (level == 2) {
+            launch_level2(pts, n, p->pass, ab_level, status, st);
+            launches++;
+        } else if (seg) {
             // small merges on this level's usual kernel, large ones in time windows
             const int min_ev = seg_min_events_at(p, n, level);
             if (level >= default_cmp_level(p, L)) {
@@ -386,7 +413,7 @@ int enqueue_hull(hull3d_plan_s *p, const int32_t *d_xyz, int64_t n, int32_t *d_f
                 launches++;
             } else {
                 launches += launch_level(pts, n, level, p->pass, 2, status, st, default_occupancy(p, level), min_ev,
-                                         level_order(p, level, &ord));
+                                         level_order(p, level, &ord), ab_level);
             }
             launch_seg_level(pts, n, level, p->pass, p->seg, p->pk0, p->pv0, p->pk1, p->pv1, p->npairs, p->overflow,
                              p->pair_cap, p->S_cap, p->M_cap, default_seg_events(p), default_seg_events_min(p),
@@ -399,7 +426,7 @@ int enqueue_hull(hull3d_plan_s *p, const int32_t *d_xyz, int64_t n, int32_t *d_f
                 launches += (last_lo + (1ll << (level - 1)) >= n) ? 2 : 1;  // level + pass-through copy
             } else {
                 launches += launch_level(pts, n, level, p->pass, 2, status, st, default_occupancy(p, level), -1,
-                                         level_order(p, level, &ord));
+                                         level_order(p, level, &ord), ab_level);
             }
         }
         if (p->profile) {
@@ -499,7 +526,10 @@ int hull3d_plan(hull3d_plan_t *out, int64_t max_n, int64_t max_clouds, const hul
     cudaGetDevice(&p->device);
     kernel_attributes();
     cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
-    p->pool_bytes = layout(p, nullptr);
+    {
+        AdjScratch as{};
+        p->pool_bytes = std::max(layout(p, nullptr), adj_layout(p, nullptr, &as));
+    }
     cudaError_t e = cudaMalloc((void **)&p->pool, p->pool_bytes);
     if (e != cudaSuccess) {
         g_last_cuda = (int)e;
@@ -671,6 +701,30 @@ int hull3d_batch_async(hull3d_plan_t p, const int32_t *d_xyz, const int64_t *h_o
     return HULL3D_OK;
 }
 
+int hull3d_adjacency_async(hull3d_plan_t p, const int32_t *d_faces, const int64_t *d_nfaces, int64_t cap_faces,
+                           int64_t n, int32_t *d_nb, int64_t *d_star_off, int32_t *d_star, int32_t *d_status,
+                           void *stream)
+{
+    if (!p || !d_nfaces || !d_star_off || !d_status || n < 1 || n > p->max_n || cap_faces < 0 ||
+        cap_faces > 2 * p->max_n)
+        return HULL3D_ERR_INVALID_ARG;
+    if (cap_faces > 0 && (!d_faces || !d_nb || !d_star)) return HULL3D_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(d_status, 0, sizeof(int32_t), st));
+    if (cap_faces == 0) {  // no faces: every star is empty
+        CK(cudaMemsetAsync(d_star_off, 0, sizeof(int64_t) * (size_t)(n + 1), st));
+        p->last_launches = 0;
+        return HULL3D_OK;
+    }
+    AdjScratch as{};
+    adj_layout(p, p->pool, &as);
+    int64_t launches = 0;
+    launch_adjacency(d_faces, d_nfaces, cap_faces, n, d_nb, d_star_off, d_star, d_status, as, p->sms, st, &launches);
+    p->last_launches = launches;
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HULL3D_OK : cuda_fail(e);
+}
+
 int hull3d_profile(hull3d_plan_t p, int enable)
 {
     if (!p) return HULL3D_ERR_INVALID_ARG;
@@ -797,6 +851,7 @@ const char *hull3d_strerror(int code)
     case HULL3D_ERR_CUDA: return "CUDA runtime error";
     case HULL3D_ERR_INTERNAL: return "internal consistency check failed";
     case HULL3D_ERR_TOO_LARGE: return "n above HULL3D_STATIC_MAX_N for the allocation-free entry point";
+    case HULL3D_ERR_NOT_CLOSED: return "faces are not a closed, consistently oriented surface";
     default: return "unknown error";
     }
 }

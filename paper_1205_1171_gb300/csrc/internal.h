@@ -43,8 +43,10 @@ struct Points {
     const int4 *P;  // [n]: (x, y, z, input index) by rank
 };
 
-// Level 1 (pairs) for both passes: links of each pair, empty movies.
-void launch_level1(int64_t n, PassBufs *passes, int npass, int32_t *status, cudaStream_t st);
+// Levels 1 and 2 for both passes: the pairs' links, then each node of four
+// ranks merges its two pairs (movies in buffer 0; event neighbours kept from
+// level ab_level on and for the last node).
+void launch_level2(const Points &pts, int64_t n, PassBufs *passes, int ab_level, int32_t *status, cudaStream_t st);
 
 // Levels [l0 + 1, l1] fused in shared memory (block = 2^l1 ranks), reading level l0 from buffer l0 & 1.
 void launch_fused(const Points &pts, int64_t n, int l0, int l1, PassBufs *passes, int npass, int32_t *status,
@@ -61,9 +63,12 @@ struct LevelOrder {
 // One level (>= 2), one thread per merge, global memory.  With max_events >= 0
 // only merges of at most max_events child events are done (see launch_level_cmp).
 // With ord, the merges of both passes run in order of decreasing child event
-// count.  Returns the number of kernel launches.
+// count.  Parent movies keep their event neighbours (A, B) only from level
+// ab_level on and for the last node of the level (see k_level).  Returns the
+// number of kernel launches.
 int launch_level(const Points &pts, int64_t n, int level, PassBufs *passes, int npass, int32_t *status,
-                 cudaStream_t st, int occupancy, int max_events = -1, const LevelOrder *ord = nullptr);
+                 cudaStream_t st, int occupancy, int max_events = -1, const LevelOrder *ord = nullptr,
+                 int ab_level = 0);
 
 // One level (>= 2), one warp per merge on a compacted shared-memory table of
 // up to scap slots (merges that do not fit run the global-memory merge).
@@ -102,6 +107,25 @@ void merge_kernel_attributes();
 void sort_kernel_attributes();
 void seg_kernel_attributes();
 void batch_kernel_attributes();
+
+// Scratch of the adjacency kernels: the directed-edge keys and edge ids
+// (two ping-pong copies of 3 F entries), their radix-sort histograms and the
+// device edge count 3 F.
+struct AdjScratch {
+    uint64_t *k0, *k1;
+    uint32_t *v0, *v1;
+    int64_t *n3;
+    SortScratch ss;
+};
+
+// Face neighbours and vertex stars of the canonical face list faces[0, *d_nf)
+// (cap rows) of a hull whose vertices are in [0, n): nb[3 f + k] is the face
+// holding the edge f[(k + 1) % 3] -> f[k]; star[star_off[v] .. star_off[v + 1])
+// are the faces around v, counter-clockwise from outside, starting from the
+// smallest.  Returns 0 and the number of launches in *launches.
+int launch_adjacency(const int32_t *faces, const int64_t *d_nf, int64_t cap, int64_t n, int32_t *nb,
+                     int64_t *star_off, int32_t *star, int32_t *status, const AdjScratch &s, int sms,
+                     cudaStream_t st, int64_t *launches);
 
 // Batched clouds: size class c (0 .. BATCH_CLASSES - 1) holds clouds of at most
 // batch_class_limit(c) points; one persistent launch hulls `count` clouds

@@ -19,30 +19,6 @@ __device__ __forceinline__ void set_status2(int32_t *status, int code) { atomicC
 size_t fused_smem_bytes(int l1);
 
 // ---------------------------------------------------------------------------
-// Level 1: pairs.  A pair's hull is its segment at every time: no events.
-// ---------------------------------------------------------------------------
-__global__ void k_level1(int64_t n, PassBufs p0, PassBufs p1, int32_t *status)
-{
-    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    const bool up = blockIdx.y != 0;
-    int2 *lk = up ? p1.lk : p0.lk;
-    int *cnt = up ? p1.cnt[1] : p0.cnt[1];
-    if ((r & 1) == 0) {
-        lk[r] = make_int2(NIL, (r + 1 < n) ? (int)(r + 1) : NIL);
-        cnt[r] = 0;
-    } else {
-        lk[r] = make_int2((int)(r - 1), NIL);
-    }
-}
-
-void launch_level1(int64_t n, PassBufs *passes, int npass, int32_t *status, cudaStream_t st)
-{
-    dim3 g((unsigned)((n + 255) / 256), npass);
-    k_level1<<<g, 256, 0, st>>>(n, passes[0], passes[npass - 1], status);
-}
-
-// ---------------------------------------------------------------------------
 // One level in global memory, one thread per merge.
 // ---------------------------------------------------------------------------
 // The event loop's candidates live in shared memory (cand_smem_bytes of
@@ -54,6 +30,48 @@ __device__ __forceinline__ void count_events(unsigned long long *lev_events, int
     const unsigned m = __activemask();
     const unsigned sum = __reduce_add_sync(m, (unsigned)k);
     if ((int)(threadIdx.x & 31) == __ffs(m) - 1 && sum) atomicAdd(lev_events + level, (unsigned long long)sum);
+}
+
+// ---------------------------------------------------------------------------
+// Levels 1 and 2 in one launch: one thread per (pass, node of four ranks)
+// links the node's pairs (the state after level 1) and merges them
+// (kinetic_merge_pairs).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_level2(Points pts, int64_t n, PassBufs p0, PassBufs p1, int ab_level,
+                                                int32_t *status)
+{
+    if (*status) return;
+    const int64_t lo = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) << 2;
+    if (lo >= n) return;
+    const bool upper = blockIdx.y != 0;
+    const PassBufs &pb = upper ? p1 : p0;
+    const int m = (int)((lo + 4 < n) ? 4 : n - lo);
+    const int r0 = (int)lo;
+    int2 *glk = pb.lk;
+    glk[r0] = make_int2(NIL, m > 1 ? r0 + 1 : NIL);
+    if (m > 1) glk[r0 + 1] = make_int2(r0, NIL);
+    if (m > 2) glk[r0 + 2] = make_int2(NIL, m > 3 ? r0 + 3 : NIL);
+    if (m > 3) glk[r0 + 3] = make_int2(r0 + 2, NIL);
+    int *cdst = pb.cnt[0];  // level 2 writes buffer 0
+    if (m <= 2) {  // no right child: the pair's (or point's) empty movie passes through
+        cdst[lo] = 0;
+        return;
+    }
+    GPts gp{ pts.P };
+    GLinks lk{ glk };
+    const bool keep_ab = 2 >= ab_level || lo + m == n;
+    GEvOut out{ pb.W[0] + 2 * lo, keep_ab ? pb.A[0] + 2 * lo : nullptr, keep_ab ? pb.B[0] + 2 * lo : nullptr };
+    int err = 0;
+    const int k = kinetic_merge_pairs(gp, lk, r0, m, out, upper, &err);
+    cdst[lo] = k;
+    if (err) set_status2(status, HULL3D_ERR_INTERNAL);
+    count_events(pb.lev_events, 2, k);
+}
+
+void launch_level2(const Points &pts, int64_t n, PassBufs *passes, int ab_level, int32_t *status, cudaStream_t st)
+{
+    const int64_t nodes = (n + 3) >> 2;
+    k_level2<<<dim3((unsigned)((nodes + 127) / 128), 2), 128, 0, st>>>(pts, n, passes[0], passes[1], ab_level, status);
 }
 
 // Merge order of one level: the (pass, node) entries sorted by the merge's
@@ -82,10 +100,14 @@ __global__ void k_order_keys(int64_t n, int level, PassBufs p0, PassBufs p1, int
 
 // order == nullptr: merge (pass = blockIdx.y, node = thread index); else the
 // thread's entry of the sorted merge order.
+// The event neighbours (A, B) of a parent movie are kept only from level
+// ab_level on and for the node that ends at n: the time-window kernels read
+// them from the children of their merges, the faces from the root movie, and
+// the last node of a level is the one a pass-through copy may carry upwards.
 template <int MINB>
 __global__ void __launch_bounds__(128, MINB) k_level(Points pts, int64_t n, int level, PassBufs p0, PassBufs p1,
                                                      int max_events, const uint32_t *order, int64_t entries,
-                                                     int32_t *status)
+                                                     int ab_level, int32_t *status)
 {
     if (*status) return;
     int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -112,7 +134,8 @@ __global__ void __launch_bounds__(128, MINB) k_level(Points pts, int64_t n, int 
     GPts gp{ pts.P };
     GLinks lk{ upper ? p1.lk : p0.lk };
     GEvIn L{ Wsrc + 2 * lo }, R{ Wsrc + 2 * mid };
-    GEvOut out{ Wdst + 2 * lo, Adst + 2 * lo, Bdst + 2 * lo };
+    const bool keep_ab = level >= ab_level || hi == n;
+    GEvOut out{ Wdst + 2 * lo, keep_ab ? Adst + 2 * lo : nullptr, keep_ab ? Bdst + 2 * lo : nullptr };
     int err = 0;
     extern __shared__ long long cand_sm[];  // the block's event-loop candidates
     const CandSmem cs{ (int *)(cand_sm + 3 * 6 * blockDim.x), cand_sm, (int)blockDim.x, (int)threadIdx.x };
@@ -143,7 +166,7 @@ __global__ void k_passthrough(int64_t lo, int level, PassBufs p0, PassBufs p1, i
 }
 
 int launch_level(const Points &pts, int64_t n, int level, PassBufs *passes, int npass, int32_t *status,
-                 cudaStream_t st, int occupancy, int max_events, const LevelOrder *ord)
+                 cudaStream_t st, int occupancy, int max_events, const LevelOrder *ord, int ab_level)
 {
     int launches = 0;
     int64_t nodes = (n + (1ll << level) - 1) >> level;
@@ -163,10 +186,11 @@ int launch_level(const Points &pts, int64_t n, int level, PassBufs *passes, int 
     const int sm = cand_smem_bytes(128);
     const Points &P = pts;
     PassBufs &a = passes[0], &b = passes[npass - 1];
-    if (occupancy >= 4) k_level<4><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, order, entries, status);
-    else if (occupancy == 3) k_level<3><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, order, entries, status);
-    else if (occupancy == 2) k_level<2><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, order, entries, status);
-    else k_level<1><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, order, entries, status);
+    const int ab = ab_level;
+    if (occupancy >= 4) k_level<4><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, order, entries, ab, status);
+    else if (occupancy == 3) k_level<3><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, order, entries, ab, status);
+    else if (occupancy == 2) k_level<2><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, order, entries, ab, status);
+    else k_level<1><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, order, entries, ab, status);
     launches++;
     int64_t lo = (nodes - 1) << level;
     if (max_events < 0 && lo + (1ll << (level - 1)) >= n) {

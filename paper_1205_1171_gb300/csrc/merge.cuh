@@ -255,6 +255,7 @@ __device__ int kinetic_forward_sm(const PT &pt, LK &lk, int &u, int &v, const EI
 #pragma unroll
     for (int l = 0; l < 6; l++) c.fi(0, l) = c.fi(1, l) = c.fi(2, l) = -2;  // no triple yet
     Tri old;
+    old.p = old.q = old.r = -2;
     bool have_old = false;
     int i = 0, j = 0, k = 0;
     for (;;) {
@@ -285,10 +286,23 @@ __device__ int kinetic_forward_sm(const PT &pt, LK &lk, int &u, int &v, const EI
             chg &= chg - 1;
             int tp, tq, tr;
             trip(l, tp, tq, tr);
+            if (tp == old.p && tq == old.q && tr == old.r) {
+                // the reverse of the bridge move just applied: the same triple
+                // as the last event, never strictly after it.  Only its
+                // triple is kept (for the change test); it stays invalid
+                // until its triple changes, which rebuilds it.
+                c.fi(0, l) = tp; c.fi(1, l) = tq; c.fi(2, l) = tr;
+                valid &= ~(1u << l);
+                continue;
+            }
             Tri t;
             tri_make(pt, t, tp, tq, tr);
             c.set(l, t);
-            bool ok = t.s != 0 && (!have_old || tri_cmp(pt, t, old, upper) > 0);
+            // a child's next event changes only right after an event of that
+            // child was taken (act rewrites links inside one child only), and
+            // a child's movie is in time order: it is always later than the
+            // last event, so only the bridge moves need the comparison
+            bool ok = t.s != 0 && (l <= 1 || !have_old || tri_cmp(pt, t, old, upper) > 0);
             valid = ok ? (valid | (1u << l)) : (valid & ~(1u << l));
         }
         int best = -1;
@@ -505,6 +519,64 @@ __device__ int kinetic_merge_sm(const PT &pt, LK &lk, int u0, int v0, int mid, c
     return k;
 }
 
+// The merge of a level-2 node: ranks r0 .. r0 + m - 1 (m = 3 or 4), children
+// the pair (r0, r0 + 1) and the pair (r0 + 2, r0 + 3) (a single point when
+// m = 3), linked as such on entry.  A pair's hull is its segment at every
+// time, so neither child has an event and of the six candidates of the merge
+// step only the two bridge triples remain: (r0, r0 + 1, v) for u stepping
+// between r0 and r0 + 1, and (u, r0 + 2, r0 + 3) for v stepping between
+// r0 + 2 and r0 + 3.  Same steps and output as kinetic_merge (at most
+// 2 m - 5 = 3 events).
+template <class PT, class LK, class EOUT>
+__device__ int kinetic_merge_pairs(const PT &pt, LK &lk, int r0, int m, EOUT &out, bool upper, int *err)
+{
+    int u = r0 + 1, v = r0 + 2;
+    bridge_walk(pt, lk, u, v, (const Tri *)nullptr, upper);  // 1. bridge at t = -inf
+    const bool has3 = m > 3;
+    Tri tu, tv, old;
+    old.p = old.q = old.r = -2;
+    bool have_old = false, vu = false, vv = false, new_u = true, new_v = true;
+    int k = 0;
+    for (;;) {  // 2. forward pass
+        // a triple is rebuilt only when the other bridge end moved; the one
+        // just applied stays invalid (its time is the last event's)
+        if (new_u) {
+            tri_make(pt, tu, r0, r0 + 1, v);
+            vu = !have_old || tri_cmp(pt, tu, old, upper) > 0;
+            new_u = false;
+        }
+        if (new_v) {
+            vv = false;
+            if (has3) {
+                tri_make(pt, tv, u, r0 + 2, r0 + 3);
+                vv = !have_old || tri_cmp(pt, tv, old, upper) > 0;
+            }
+            new_v = false;
+        }
+        const bool take_u = vu && (!vv || tri_cmp(pt, tu, tv, upper) < 0);
+        if (!take_u && !vv) break;
+        if (k >= 2 * m) { *err = 1; return k; }
+        if (take_u) {  // r0 + 1 joins the bridge (u advances) or leaves it (u retreats)
+            const bool ins = u == r0;
+            out.put(k++, (unsigned)(r0 + 1) | (ins ? INS_BIT : 0u), r0, v);
+            u = ins ? r0 + 1 : r0;
+            old = tu;
+            vu = false;
+            new_v = true;
+        } else {  // r0 + 2 joins the bridge (v retreats) or leaves it (v advances)
+            const bool ins = v == r0 + 3;
+            out.put(k++, (unsigned)(r0 + 2) | (ins ? INS_BIT : 0u), u, r0 + 3);
+            v = ins ? r0 + 2 : r0 + 3;
+            old = tv;
+            vv = false;
+            new_u = true;
+        }
+        have_old = true;
+    }
+    kinetic_backward(pt, lk, u, v, r0 + 2, out, k);  // 3.
+    return k;
+}
+
 // ---- storage adapters -------------------------------------------------------
 // Points are packed as int4 (x, y, z, input index); links as int2 (prev, next).
 
@@ -533,10 +605,14 @@ struct GEvIn {  // a movie in global memory
     __device__ __forceinline__ unsigned w(int i) const { return W[i]; }
 };
 
-struct GEvOut {
+struct GEvOut {  // A == nullptr: the neighbours are not kept (no later reader)
     unsigned *W;
     int *A, *B;
-    __device__ __forceinline__ void put(int k, unsigned w, int a, int b) { W[k] = w; A[k] = a; B[k] = b; }
+    __device__ __forceinline__ void put(int k, unsigned w, int a, int b)
+    {
+        W[k] = w;
+        if (A) { A[k] = a; B[k] = b; }
+    }
     __device__ __forceinline__ unsigned w(int k) const { return W[k]; }
 };
 

@@ -28,13 +28,15 @@ ERR_DEVICE_TIMEOUT = 7
 ERR_CUDA = 8
 ERR_INTERNAL = 9
 ERR_TOO_LARGE = 10
+ERR_NOT_CLOSED = 11
 STATIC_MAX_N = 16384
 
 # every symbol include/hull3d.h declares
 EXPORTS = (
     "hull3d_plan", "hull3d_plan_opts", "hull3d_destroy", "hull3d_plan_bytes", "hull3d_compute_async", "hull3d_compute",
     "hull3d_compute_host", "hull3d_batch_async", "hull3d_strerror", "hull3d_last_cuda_error",
-    "hull3d_last_launch_count", "hull3d_compute_static", "hull3d_profile", "hull3d_profile_read", "hull3d_profile_levels", "hull3d_level_events",
+    "hull3d_last_launch_count", "hull3d_compute_static", "hull3d_profile", "hull3d_profile_read", "hull3d_profile_levels",
+    "hull3d_level_events", "hull3d_adjacency_async",
 )
 PHASES = ("sort", "fused", "levels", "seg", "faces")
 
@@ -82,6 +84,8 @@ def load():
             lib.hull3d_compute_host.restype = ctypes.c_int
             lib.hull3d_batch_async.argtypes = [P, P, P, i64, P, P, P, P, P]
             lib.hull3d_batch_async.restype = ctypes.c_int
+            lib.hull3d_adjacency_async.argtypes = [P, P, P, i64, i64, P, P, P, P, P]
+            lib.hull3d_adjacency_async.restype = ctypes.c_int
             lib.hull3d_compute_static.argtypes = [P, i64, P, i64, P, P, P]
             lib.hull3d_compute_static.restype = ctypes.c_int
             lib.hull3d_strerror.argtypes = [ctypes.c_int]
@@ -268,6 +272,42 @@ class Hull3D:
                                           _stream_ptr(stream))
         if rc:
             raise Hull3DError(rc, "batch_async")
+
+    def adjacency_async(self, faces, d_nfaces, n: int, nb, star_off, star, d_status, stream=None) -> None:
+        """Enqueues the face neighbours and vertex stars of the canonical face
+        list faces[:d_nfaces] ((cap, 3) int32 device tensor, vertices in [0, n)):
+        nb (cap, 3) int32, star_off (n + 1) int64 and star (3 cap) int32 device
+        tensors are written; d_status gets 0 or ERR_NOT_CLOSED."""
+        cap = int(faces.shape[0])
+        rc = self._lib.hull3d_adjacency_async(self._plan, faces.data_ptr(), d_nfaces.data_ptr(), cap, int(n),
+                                              nb.data_ptr(), star_off.data_ptr(), star.data_ptr(),
+                                              d_status.data_ptr(), _stream_ptr(stream))
+        if rc:
+            raise Hull3DError(rc, "adjacency_async")
+
+    def adjacency(self, faces, n: int, stream=None):
+        """(nb (F, 3) int32, star_off (n + 1) int64, star (3 F) int32) on the
+        device of the canonical (F, 3) int32 face tensor (synchronous)."""
+        import torch
+
+        F = int(faces.shape[0])
+        dev = faces.device
+        if F == 0:
+            faces = torch.zeros((1, 3), dtype=torch.int32, device=dev)
+        d_nf = torch.tensor([F], dtype=torch.int64, device=dev)
+        nb = torch.empty((max(F, 1), 3), dtype=torch.int32, device=dev)
+        off = torch.empty(int(n) + 1, dtype=torch.int64, device=dev)
+        star = torch.empty(max(3 * F, 1), dtype=torch.int32, device=dev)
+        st = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.adjacency_async(faces.contiguous(), d_nf, n, nb, off, star, st, stream)
+        if stream is None:
+            torch.cuda.current_stream(dev).synchronize()
+        else:
+            stream.synchronize()
+        code = int(st.item())
+        if code:
+            raise Hull3DError(code, "adjacency")
+        return nb[:F], off, star[: 3 * F]
 
     def batch(self, xyz, offsets: np.ndarray, stream=None):
         """Hulls of B clouds; returns (faces, face_offsets, nfaces, status) with

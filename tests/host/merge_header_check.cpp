@@ -3,8 +3,11 @@
 // point set level by level exactly as the device driver orders them (aligned
 // blocks, both passes, faces from the root movies):
 //   form 0: kinetic_merge, the loop the batch kernel and the serial fallback run;
-//   form 1: kinetic_merge_sm, the loop of the thread-per-merge level kernel,
-//           with its candidates in a one-thread CandSmem slice;
+//   form 1: kinetic_merge_pairs at level 2 and kinetic_merge_sm above it, the
+//           loops of the level kernels, with the candidates in a one-thread
+//           CandSmem slice and event neighbours kept only at the root and for
+//           the last node of each level (the rule of the level kernels when no
+//           time windows read them);
 // and, from cmp_level on (> 0), the compacted slot-table form of the
 // warp-per-merge kernel.  tests/test_merge_header_host.py compares the faces
 // with the oracle's.
@@ -167,7 +170,10 @@ extern "C" int merge_header_hull(const int32_t *xyz, int64_t n, int form, int cm
                 } else {
                     GEvIn Lv{ W[src].data() + 2 * lo }, Rv{ W[src].data() + 2 * mid };
                     GEvOut out{ W[dst].data() + 2 * lo, A[dst].data() + 2 * lo, B[dst].data() + 2 * lo };
-                    if (form == 1)
+                    if (form == 1 && level < L && hi != n) out.A = out.B = nullptr;  // the level kernel's rule
+                    if (form == 1 && level == 2)
+                        k = kinetic_merge_pairs(gp, gl, (int)lo, (int)(hi - lo), out, upper, &err);
+                    else if (form == 1)
                         k = kinetic_merge_sm(gp, gl, (int)mid - 1, (int)mid, (int)mid, Lv, nl, Rv, nr, out,
                                              (int)(2 * (hi - lo)), upper, &err, cs);
                     else
