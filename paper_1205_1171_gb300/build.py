@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhull3d.so")
-SOURCES = ["api.cu", "sort.cu", "merge.cu", "segmerge.cu", "batch.cu", "adjacency.cu"]
+SOURCES = ["api.cu", "sort.cu", "merge.cu", "segmerge.cu", "batch.cu", "adjacency.cu", "multi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -124,6 +124,9 @@ struct hull3d_plan_s {
     int *b_counter = nullptr;
     std::vector<int32_t> h_order;
     int sms = 0;
+    // groups of large clouds hulled together (multi.cu)
+    MultiTables mt{};
+    int64_t mt_cap = 0;  // clouds per group
 };
 
 namespace {
@@ -233,6 +236,19 @@ size_t layout(hull3d_plan_s *p, char *base)
             }
         }
     }
+    // tables of a group of large clouds: blocks of at least 2^SPAN_SHIFT ranks
+    p->mt_cap = (N >> SPAN_SHIFT) + 1;
+    p->mt.blk = b.take<int32_t>(p->mt_cap);
+    p->mt.cbase = b.take<int64_t>(p->mt_cap);
+    p->mt.cend = b.take<int64_t>(p->mt_cap);
+    p->mt.coff = b.take<int64_t>(p->mt_cap + 1);
+    p->mt.ioff = b.take<int64_t>(p->mt_cap);
+    p->mt.cfoff = b.take<int64_t>(p->mt_cap);
+    p->mt.ctop = b.take<int32_t>(p->mt_cap);
+    p->mt.cstat = b.take<int32_t>(p->mt_cap);
+    p->mt.corig = b.take<int32_t>(p->mt_cap);
+    p->mt.fcount = b.take<int64_t>(p->mt_cap);
+    p->mt.fstart = b.take<int64_t>(p->mt_cap + 1);
     p->lev_stats = b.take<unsigned long long>(128);
     p->b_off = b.take<int64_t>(p->max_clouds + 1);
     p->b_foff = b.take<int64_t>(p->max_clouds + 1);
@@ -353,6 +369,58 @@ int mark(hull3d_plan_s *p, cudaStream_t st, int *slot)
         if (rc_) return rc_;                         \
     } while (0)
 
+// Enqueues merge levels l1 + 1 .. L over the rank space sp (one cloud, or
+// ncl clouds in aligned blocks): one launch sequence per level for every
+// node of every cloud at that level, with no host synchronisation.
+int enqueue_levels(hull3d_plan_s *p, const Points &pts, const Span &sp, int ncl, int L, int l1, int32_t *status,
+                   cudaStream_t st, int64_t *launches, int *slots, bool *seg_marked)
+{
+    const int64_t R = sp.n;  // the rank space: thresholds follow the merges a level holds
+    const LevelOrder ord{ p->k0, p->k1, p->v0, p->v1, p->ss };
+    // parent movies keep their event neighbours from the level below the
+    // first time-window level (whose kernels read them) and at the roots
+    const int ab_level = p->S_cap ? std::min(default_seg_level(p) - 1, L) : L;
+    const int LR = ceil_log2(R);
+    for (int level = l1 + 1; level <= L; level++) {
+        // level 2 merges event-free pairs: its own kernel, never time windows
+        const bool seg = level >= default_seg_level(p) && p->S_cap && level > 2;
+        if (seg && !*seg_marked) { MARK(3); *seg_marked = true; }
+        int lv0 = -1, lv1 = -1;
+        if (p->profile) { int r_ = mark(p, st, &lv0); if (r_) return r_; }
+        if (level == 2) {
+            launch_level2(pts, sp, p->pass, ab_level, status, st);
+            *launches += 1;
+        } else if (seg) {
+            // small merges on this level's usual kernel, large ones in time windows
+            const int min_ev = seg_min_events_at(p, R, level);
+            if (level >= default_cmp_level(p, LR)) {
+                launch_level_cmp(pts, sp, level, p->pass, 2, status, st, cmp_slots_at(p, min_ev), min_ev);
+                *launches += 1;
+            } else {
+                *launches += launch_level(pts, sp, level, p->pass, 2, status, st, default_occupancy(p, level), min_ev,
+                                          level_order(p, level, &ord), ab_level);
+            }
+            launch_seg_level(pts, sp, level, p->pass, p->seg, p->pk0, p->pv0, p->pk1, p->pv1, p->npairs, p->overflow,
+                             p->pair_cap, p->S_cap, p->M_cap, default_seg_events(p), default_seg_events_min(p),
+                             default_seg_slots(p), min_ev, p->ss, status, st, launches);
+        } else if (level >= default_cmp_level(p, LR)) {
+            launch_level_cmp(pts, sp, level, p->pass, 2, status, st, default_cmp_slots(p));
+            *launches += 1;
+        } else {
+            *launches += launch_level(pts, sp, level, p->pass, 2, status, st, default_occupancy(p, level), -1,
+                                      level_order(p, level, &ord), ab_level);
+        }
+        if (level > 2) *launches += launch_passthrough(sp, ncl, level, p->pass, status, st);
+        if (p->profile) {
+            int r_ = mark(p, st, &lv1);
+            if (r_) return r_;
+            p->level_marks.insert(p->level_marks.end(), { level, lv0, lv1 });
+        }
+        STEP("merge level");
+    }
+    return HULL3D_OK;
+}
+
 // Enqueues the whole single-hull pipeline.
 int enqueue_hull(hull3d_plan_s *p, const int32_t *d_xyz, int64_t n, int32_t *d_faces, int64_t *nf, int32_t *status,
                  cudaStream_t st)
@@ -392,49 +460,9 @@ int enqueue_hull(hull3d_plan_s *p, const int32_t *d_xyz, int64_t n, int32_t *d_f
     STEP("fused levels");
     MARK(2);
     bool seg_marked = false;
-    const LevelOrder ord{ p->k0, p->k1, p->v0, p->v1, p->ss };
-    // parent movies keep their event neighbours from the level below the
-    // first time-window level (whose kernels read them) and at the root
-    const int ab_level = p->S_cap ? std::min(default_seg_level(p) - 1, L) : L;
-    for (int level = l1 + 1; level <= L; level++) {
-        // level 2 merges event-free pairs: its own kernel, never time windows
-        const bool seg = level >= default_seg_level(p) && p->S_cap && level > 2;
-        if (seg && !seg_marked) { MARK(3); seg_marked = true; }
-        int lv0 = -1, lv1 = -1;
-        if (p->profile) { int r_ = mark(p, st, &lv0); if (r_) return r_; }
-        if (level == 2) {
-            launch_level2(pts, n, p->pass, ab_level, status, st);
-            launches++;
-        } else if (seg) {
-            // small merges on this level's usual kernel, large ones in time windows
-            const int min_ev = seg_min_events_at(p, n, level);
-            if (level >= default_cmp_level(p, L)) {
-                launch_level_cmp(pts, n, level, p->pass, 2, status, st, cmp_slots_at(p, min_ev), min_ev);
-                launches++;
-            } else {
-                launches += launch_level(pts, n, level, p->pass, 2, status, st, default_occupancy(p, level), min_ev,
-                                         level_order(p, level, &ord), ab_level);
-            }
-            launch_seg_level(pts, n, level, p->pass, p->seg, p->pk0, p->pv0, p->pk1, p->pv1, p->npairs, p->overflow,
-                             p->pair_cap, p->S_cap, p->M_cap, default_seg_events(p), default_seg_events_min(p),
-                             default_seg_slots(p), min_ev, p->ss,
-                             status, st, &launches);
-        } else {
-            if (level >= default_cmp_level(p, L)) {
-                launch_level_cmp(pts, n, level, p->pass, 2, status, st, default_cmp_slots(p));
-                int64_t last_lo = (((n + (1ll << level) - 1) >> level) - 1) << level;
-                launches += (last_lo + (1ll << (level - 1)) >= n) ? 2 : 1;  // level + pass-through copy
-            } else {
-                launches += launch_level(pts, n, level, p->pass, 2, status, st, default_occupancy(p, level), -1,
-                                         level_order(p, level, &ord), ab_level);
-            }
-        }
-        if (p->profile) {
-            int r_ = mark(p, st, &lv1);
-            if (r_) return r_;
-            p->level_marks.insert(p->level_marks.end(), { level, lv0, lv1 });
-        }
-        STEP("merge level");
+    {
+        int rc = enqueue_levels(p, pts, single_span(n), 1, L, l1, status, st, &launches, slots, &seg_marked);
+        if (rc) return rc;
     }
     if (!seg_marked) MARK(3);
     MARK(4);
@@ -454,6 +482,82 @@ int enqueue_hull(hull3d_plan_s *p, const int32_t *d_xyz, int64_t n, int32_t *d_f
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
     return HULL3D_OK;
+}
+
+// Largest cloud the multi-cloud path takes (face keys need the cloud index
+// and two vertex indices in 64 bits).
+constexpr int64_t MULTI_MAX_CLOUD = 1ll << 24;
+
+int64_t pow2_ceil(int64_t x)
+{
+    int64_t b = 1;
+    while (b < x) b <<= 1;
+    return b;
+}
+
+// Enqueues the hulls of the clouds group[0 .. C) (batch indices, decreasing
+// size, each of more than 4096 points, their aligned blocks fitting the
+// plan's max_n ranks) together: one sort, one launch sequence per merge
+// level for all of them, one face sort.
+int enqueue_multi(hull3d_plan_s *p, const int32_t *d_xyz, const int64_t *h_offsets, const int64_t *h_face_offsets,
+                  const std::vector<int32_t> &group, int32_t *d_faces, int64_t *d_nfaces, int32_t *d_status,
+                  cudaStream_t st, int64_t *launches)
+{
+    const int C = (int)group.size();
+    std::vector<int64_t> cbase(C), cend(C), coff(C + 1), ioff(C), cfoff(C);
+    std::vector<int32_t> ctop(C), corig(C);
+    int64_t R = 0, total = 0, nmax = 0;
+    int L = 0;
+    for (int c = 0; c < C; c++) {
+        const int32_t b = group[c];
+        const int64_t nb = h_offsets[b + 1] - h_offsets[b];
+        const int64_t blk = pow2_ceil(nb);  // blocks by decreasing size: each starts at a multiple of its size
+        cbase[c] = R;
+        cend[c] = R + nb;
+        coff[c] = total;
+        ioff[c] = h_offsets[b];
+        cfoff[c] = h_face_offsets[b];
+        ctop[c] = ceil_log2(nb);
+        corig[c] = b;
+        R += blk;
+        total += nb;
+        nmax = std::max(nmax, nb);
+        L = std::max(L, ctop[c]);
+    }
+    coff[C] = total;
+    std::vector<int32_t> blkmap((size_t)(R >> SPAN_SHIFT), -1);
+    for (int c = 0; c < C; c++)
+        for (int64_t r = cbase[c]; r < cbase[c] + pow2_ceil(cend[c] - cbase[c]); r += 1ll << SPAN_SHIFT)
+            blkmap[(size_t)(r >> SPAN_SHIFT)] = c;
+    MultiTables t = p->mt;
+    t.ncl = C;
+    CK(cudaMemcpyAsync(t.blk, blkmap.data(), sizeof(int32_t) * blkmap.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(t.cbase, cbase.data(), sizeof(int64_t) * C, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(t.cend, cend.data(), sizeof(int64_t) * C, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(t.coff, coff.data(), sizeof(int64_t) * (C + 1), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(t.ioff, ioff.data(), sizeof(int64_t) * C, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(t.cfoff, cfoff.data(), sizeof(int64_t) * C, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(t.ctop, ctop.data(), sizeof(int32_t) * C, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(t.corig, corig.data(), sizeof(int32_t) * C, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(t.cstat, 0, sizeof(int32_t) * C, st));
+    CK(cudaMemsetAsync(p->status, 0, sizeof(int32_t), st));
+    CK(cudaMemsetAsync(p->lev_stats, 0, 128 * sizeof(unsigned long long), st));
+    launch_multi_sort(d_xyz, t, C, total, p->P4, p->k0, p->v0, p->k1, p->v1, p->ss, p->sms, st, launches);
+    const Points pts{ p->P4 };
+    const Span sp{ R, t.blk, t.cbase, t.cend, t.ctop, t.cstat };
+    // the per-call phase record belongs to single hulls: none is kept here
+    const bool prof = p->profile;
+    p->profile = false;
+    int slots[HULL3D_PHASES + 1];
+    bool seg_marked = false;
+    int rc = enqueue_levels(p, pts, sp, C, L, 1, p->status, st, launches, slots, &seg_marked);
+    p->profile = prof;
+    if (rc) return rc;
+    const int fbits = ceil_log2(nmax);
+    launch_multi_faces(pts, t, C, fbits, p->pass, p->k0, p->v0, p->k1, p->v1, 2 * p->max_n, p->ss, p->status,
+                       d_faces, d_nfaces, d_status, p->sms, st, launches);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HULL3D_OK : cuda_fail(e);
 }
 
 bool use_graphs(const hull3d_plan_s *p) { return p->opts.use_graph >= 0 && !p->profile && !debug_sync(); }
@@ -686,14 +790,41 @@ int hull3d_batch_async(hull3d_plan_t p, const int32_t *d_xyz, const int64_t *h_o
                            d_nfaces, d_status, p->sms, st);
         launches++;
     }
-    // clouds above the largest class: the plain pipeline, one after the other
-    for (int64_t q = cls_begin[BATCH_CLASSES]; q < cls_begin[BATCH_CLASSES - 1]; q++) {
-        const int32_t b = ord[q];
-        const int64_t nb = h_offsets[b + 1] - h_offsets[b];
-        int rc = enqueue_hull(p, d_xyz + 3 * h_offsets[b], nb, d_faces + 3 * h_face_offsets[b], d_nfaces + b,
-                              d_status + b, st);
+    // clouds above the largest class (ord holds them by decreasing size):
+    // hulled together, level by level, in groups whose aligned blocks fill
+    // the plan's max_n ranks; a cloud whose block alone does not fit runs
+    // the single-hull pipeline
+    {
+        std::vector<int32_t> group;
+        int64_t used = 0;
+        auto flush = [&]() -> int {
+            if (group.empty()) return HULL3D_OK;
+            int rc = enqueue_multi(p, d_xyz, h_offsets, h_face_offsets, group, d_faces, d_nfaces, d_status, st,
+                                   &launches);
+            group.clear();
+            used = 0;
+            return rc;
+        };
+        for (int64_t q = cls_begin[BATCH_CLASSES]; q < cls_begin[BATCH_CLASSES - 1]; q++) {
+            const int32_t b = ord[q];
+            const int64_t nb = h_offsets[b + 1] - h_offsets[b];
+            const int64_t blk = pow2_ceil(nb);
+            if (blk > p->max_n || nb > MULTI_MAX_CLOUD) {
+                int rc = enqueue_hull(p, d_xyz + 3 * h_offsets[b], nb, d_faces + 3 * h_face_offsets[b], d_nfaces + b,
+                                      d_status + b, st);
+                if (rc) return rc;
+                launches += p->last_launches;
+                continue;
+            }
+            if (used + blk > p->max_n || (int64_t)group.size() + 1 > p->mt_cap) {
+                int rc = flush();
+                if (rc) return rc;
+            }
+            group.push_back(b);
+            used += blk;
+        }
+        int rc = flush();
         if (rc) return rc;
-        launches += p->last_launches;
     }
     p->last_launches = launches;
     cudaError_t e = cudaGetLastError();

@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include "../../include/hull3d.h"
+#include "span.cuh"
 
 namespace hull3d {
 
@@ -46,7 +47,7 @@ struct Points {
 // Levels 1 and 2 for both passes: the pairs' links, then each node of four
 // ranks merges its two pairs (movies in buffer 0; event neighbours kept from
 // level ab_level on and for the last node).
-void launch_level2(const Points &pts, int64_t n, PassBufs *passes, int ab_level, int32_t *status, cudaStream_t st);
+void launch_level2(const Points &pts, const Span &sp, PassBufs *passes, int ab_level, int32_t *status, cudaStream_t st);
 
 // Levels [l0 + 1, l1] fused in shared memory (block = 2^l1 ranks), reading level l0 from buffer l0 & 1.
 void launch_fused(const Points &pts, int64_t n, int l0, int l1, PassBufs *passes, int npass, int32_t *status,
@@ -66,26 +67,27 @@ struct LevelOrder {
 // count.  Parent movies keep their event neighbours (A, B) only from level
 // ab_level on and for the last node of the level (see k_level).  Returns the
 // number of kernel launches.
-int launch_level(const Points &pts, int64_t n, int level, PassBufs *passes, int npass, int32_t *status,
+int launch_level(const Points &pts, const Span &sp, int level, PassBufs *passes, int npass, int32_t *status,
                  cudaStream_t st, int occupancy, int max_events = -1, const LevelOrder *ord = nullptr,
                  int ab_level = 0);
 
 // One level (>= 2), one warp per merge on a compacted shared-memory table of
 // up to scap slots (merges that do not fit run the global-memory merge).
 // With max_events >= 0 only merges of at most max_events child events are
-// done (the others are left to the time-segment kernels, which also copy the
-// pass-through node).
-void launch_level_cmp(const Points &pts, int64_t n, int level, PassBufs *passes, int npass, int32_t *status,
+// done (the others are left to the time-segment kernels).
+void launch_level_cmp(const Points &pts, const Span &sp, int level, PassBufs *passes, int npass, int32_t *status,
                       cudaStream_t st, int scap, int max_events = -1);
 
-// Copies the movie of the last node of a level when it has no right child.
-void launch_passthrough(int64_t n, int level, int64_t lo, PassBufs *passes, int32_t *status, cudaStream_t st);
+// Copies the movie of each cloud's last node of a level when it has no right
+// child (the span's ncl clouds; one cloud: only when needed).  Returns the
+// number of launches.
+int launch_passthrough(const Span &sp, int ncl, int level, PassBufs *passes, int32_t *status, cudaStream_t st);
 
 struct SegBufs;
 // One level merged time-segment-parallel (windows of Kmin .. K child events,
 // see seg_window_len; slot tables of scap points); pairs/pair_vals and their
 // alternates hold pair_cap sort items.
-void launch_seg_level(const Points &pts, int64_t n, int level, PassBufs *passes, SegBufs *sbufs, uint64_t *pairs,
+void launch_seg_level(const Points &pts, const Span &sp, int level, PassBufs *passes, SegBufs *sbufs, uint64_t *pairs,
                       uint32_t *pair_vals, uint64_t *pairs_alt, uint32_t *vals_alt, unsigned long long *npairs,
                       int *overflow, int64_t pair_cap, int64_t S_cap, int64_t M_cap, int K, int Kmin, int scap,
                       int min_events, const SortScratch &ss, int32_t *status, cudaStream_t st, int64_t *launches);
@@ -126,6 +128,32 @@ struct AdjScratch {
 int launch_adjacency(const int32_t *faces, const int64_t *d_nf, int64_t cap, int64_t n, int32_t *nb,
                      int64_t *star_off, int32_t *star, int32_t *status, const AdjScratch &s, int sms,
                      cudaStream_t st, int64_t *launches);
+
+// Device tables of a group of clouds hulled together (multi.cu): layout
+// order c = 0 .. ncl - 1 (clouds by decreasing size, each in an aligned block
+// of 2^L_c ranks), blk[] maps each 2^SPAN_SHIFT ranks to its cloud.
+struct MultiTables {
+    int ncl;
+    int32_t *blk;                                 // [rank space >> SPAN_SHIFT]
+    int64_t *cbase, *cend;                        // [ncl]: block start, block start + n_c
+    int64_t *coff;                                // [ncl + 1]: start of cloud c among the group's points
+    int64_t *ioff, *cfoff;                        // [ncl]: first input row, first output face row
+    int32_t *ctop, *cstat, *corig;                // [ncl]: L_c, input status, index in the caller's batch
+    int64_t *fcount, *fstart;                     // [ncl], [ncl + 1]: faces per cloud and their prefix
+};
+
+// Steps 1-3 of a group (see multi.cu): keys, the two stable sorts and the
+// decode into the rank space (P); total = points of the group.
+int launch_multi_sort(const int32_t *xyz, const MultiTables &t, int C, int64_t total, int4 *P, uint64_t *k0,
+                      uint32_t *v0, uint64_t *k1, uint32_t *v1, const SortScratch &ss, int sms, cudaStream_t st,
+                      int64_t *launches);
+
+// Step 5: faces of every cloud of the group into the caller's rows, face
+// counts and statuses by batch index (cap = face-key capacity of k0 .. v1).
+int launch_multi_faces(const Points &pts, const MultiTables &t, int C, int fbits, PassBufs *passes, uint64_t *k0,
+                       uint32_t *v0, uint64_t *k1, uint32_t *v1, int64_t cap, const SortScratch &ss,
+                       const int32_t *status, int32_t *faces, int64_t *nfaces, int32_t *cstatus, int sms,
+                       cudaStream_t st, int64_t *launches);
 
 // Batched clouds: size class c (0 .. BATCH_CLASSES - 1) holds clouds of at most
 // batch_class_limit(c) points; one persistent launch hulls `count` clouds

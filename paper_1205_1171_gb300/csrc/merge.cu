@@ -37,15 +37,16 @@ __device__ __forceinline__ void count_events(unsigned long long *lev_events, int
 // links the node's pairs (the state after level 1) and merges them
 // (kinetic_merge_pairs).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_level2(Points pts, int64_t n, PassBufs p0, PassBufs p1, int ab_level,
+__global__ void __launch_bounds__(128) k_level2(Points pts, Span sp, PassBufs p0, PassBufs p1, int ab_level,
                                                 int32_t *status)
 {
     if (*status) return;
     const int64_t lo = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) << 2;
-    if (lo >= n) return;
+    int64_t hi, end;
+    if (!node_span(sp, 2, lo, hi, end)) return;
     const bool upper = blockIdx.y != 0;
     const PassBufs &pb = upper ? p1 : p0;
-    const int m = (int)((lo + 4 < n) ? 4 : n - lo);
+    const int m = (int)(hi - lo);
     const int r0 = (int)lo;
     int2 *glk = pb.lk;
     glk[r0] = make_int2(NIL, m > 1 ? r0 + 1 : NIL);
@@ -59,7 +60,7 @@ __global__ void __launch_bounds__(128) k_level2(Points pts, int64_t n, PassBufs 
     }
     GPts gp{ pts.P };
     GLinks lk{ glk };
-    const bool keep_ab = 2 >= ab_level || lo + m == n;
+    const bool keep_ab = 2 >= ab_level || hi == end;
     GEvOut out{ pb.W[0] + 2 * lo, keep_ab ? pb.A[0] + 2 * lo : nullptr, keep_ab ? pb.B[0] + 2 * lo : nullptr };
     int err = 0;
     const int k = kinetic_merge_pairs(gp, lk, r0, m, out, upper, &err);
@@ -68,10 +69,11 @@ __global__ void __launch_bounds__(128) k_level2(Points pts, int64_t n, PassBufs 
     count_events(pb.lev_events, 2, k);
 }
 
-void launch_level2(const Points &pts, int64_t n, PassBufs *passes, int ab_level, int32_t *status, cudaStream_t st)
+void launch_level2(const Points &pts, const Span &sp, PassBufs *passes, int ab_level, int32_t *status, cudaStream_t st)
 {
-    const int64_t nodes = (n + 3) >> 2;
-    k_level2<<<dim3((unsigned)((nodes + 127) / 128), 2), 128, 0, st>>>(pts, n, passes[0], passes[1], ab_level, status);
+    const int64_t nodes = (sp.n + 3) >> 2;
+    k_level2<<<dim3((unsigned)((nodes + 127) / 128), 2), 128, 0, st>>>(pts, sp, passes[0], passes[1], ab_level,
+                                                                      status);
 }
 
 // Merge order of one level: the (pass, node) entries sorted by the merge's
@@ -79,7 +81,7 @@ void launch_level2(const Points &pts, int64_t n, PassBufs *passes, int ab_level,
 // quite different numbers of rounds and a warp runs as long as its longest
 // merge (about 70% of the lanes busy on a uniform cube); sorted, the 32 merges
 // of a warp take about as many rounds each.
-__global__ void k_order_keys(int64_t n, int level, PassBufs p0, PassBufs p1, int64_t nodes, uint64_t *keys,
+__global__ void k_order_keys(Span sp, int level, PassBufs p0, PassBufs p1, int64_t nodes, uint64_t *keys,
                              uint32_t *vals)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -88,8 +90,9 @@ __global__ void k_order_keys(int64_t n, int level, PassBufs p0, PassBufs p1, int
     const int64_t node = pass ? i - nodes : i;
     const int src = (level - 1) & 1;
     const int64_t lo = node << level, mid = lo + (1ll << (level - 1));
-    unsigned work = 0;  // a node without a right child sorts last (k_level skips it)
-    if (mid < n) {
+    unsigned work = 0;  // no node, or one without a right child: sorts last (k_level skips it)
+    int64_t hi;
+    if (node_span(sp, level, lo, hi) && mid < hi) {
         const int *c = (pass ? p1 : p0).cnt[src];
         const unsigned w = (unsigned)c[lo] + (unsigned)c[mid];
         work = (w < 0xfffeu ? w : 0xfffeu) + 1;
@@ -101,11 +104,12 @@ __global__ void k_order_keys(int64_t n, int level, PassBufs p0, PassBufs p1, int
 // order == nullptr: merge (pass = blockIdx.y, node = thread index); else the
 // thread's entry of the sorted merge order.
 // The event neighbours (A, B) of a parent movie are kept only from level
-// ab_level on and for the node that ends at n: the time-window kernels read
-// them from the children of their merges, the faces from the root movie, and
-// the last node of a level is the one a pass-through copy may carry upwards.
+// ab_level on and for the node that ends at its cloud's end: the time-window
+// kernels read them from the children of their merges, the faces from the
+// root movie, and the last node of a level is the one a pass-through copy may
+// carry upwards.
 template <int MINB>
-__global__ void __launch_bounds__(128, MINB) k_level(Points pts, int64_t n, int level, PassBufs p0, PassBufs p1,
+__global__ void __launch_bounds__(128, MINB) k_level(Points pts, Span sp, int level, PassBufs p0, PassBufs p1,
                                                      int max_events, const uint32_t *order, int64_t entries,
                                                      int ab_level, int32_t *status)
 {
@@ -118,11 +122,12 @@ __global__ void __launch_bounds__(128, MINB) k_level(Points pts, int64_t n, int 
         upper = (e >> 31) != 0;
         node = e & 0x7fffffffu;
     }
-    int64_t lo = node << level;
-    if (lo >= n) return;
+    const int64_t lo = node << level;
+    int64_t hi, end;
+    if (!node_span(sp, level, lo, hi, end)) return;
     const int src = (level - 1) & 1, dst = level & 1;
     const int64_t half = 1ll << (level - 1);
-    const int64_t mid = lo + half, hi = (lo + 2 * half < n) ? lo + 2 * half : n;
+    const int64_t mid = lo + half;
     if (mid >= hi) return;  // pass-through nodes are copied by k_passthrough
     const int *csrc = upper ? p1.cnt[src] : p0.cnt[src];
     int *cdst = upper ? p1.cnt[dst] : p0.cnt[dst];
@@ -134,7 +139,7 @@ __global__ void __launch_bounds__(128, MINB) k_level(Points pts, int64_t n, int 
     GPts gp{ pts.P };
     GLinks lk{ upper ? p1.lk : p0.lk };
     GEvIn L{ Wsrc + 2 * lo }, R{ Wsrc + 2 * mid };
-    const bool keep_ab = level >= ab_level || hi == n;
+    const bool keep_ab = level >= ab_level || hi == end;
     GEvOut out{ Wdst + 2 * lo, keep_ab ? Adst + 2 * lo : nullptr, keep_ab ? Bdst + 2 * lo : nullptr };
     int err = 0;
     extern __shared__ long long cand_sm[];  // the block's event-loop candidates
@@ -146,8 +151,9 @@ __global__ void __launch_bounds__(128, MINB) k_level(Points pts, int64_t n, int 
     count_events(upper ? p1.lev_events : p0.lev_events, level, k);
 }
 
-// The last node of a level may have no right child: its movie is the child's.
-__global__ void k_passthrough(int64_t lo, int level, PassBufs p0, PassBufs p1, int32_t *status)
+// The last node of a cloud's level may have no right child: its movie is the
+// child's.  bpc blocks per cloud copy it (grid.x = clouds x bpc, grid.y = pass).
+__global__ void k_passthrough(Span sp, int ncl, int bpc, int level, PassBufs p0, PassBufs p1, int32_t *status)
 {
     if (*status) return;
     const bool up = blockIdx.y != 0;
@@ -156,26 +162,55 @@ __global__ void k_passthrough(int64_t lo, int level, PassBufs p0, PassBufs p1, i
     const int *As = up ? p1.A[src] : p0.A[src], *Bs = up ? p1.B[src] : p0.B[src];
     unsigned *Wd = up ? p1.W[dst] : p0.W[dst];
     int *Ad = up ? p1.A[dst] : p0.A[dst], *Bd = up ? p1.B[dst] : p0.B[dst];
-    int c = (up ? p1.cnt[src] : p0.cnt[src])[lo];
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < c; e += (int64_t)gridDim.x * blockDim.x) {
-        Wd[2 * lo + e] = Ws[2 * lo + e];
-        Ad[2 * lo + e] = As[2 * lo + e];
-        Bd[2 * lo + e] = Bs[2 * lo + e];
+    const int *cs = up ? p1.cnt[src] : p0.cnt[src];
+    int *cd = up ? p1.cnt[dst] : p0.cnt[dst];
+    const int part = (int)blockIdx.x % bpc;
+    for (int c = (int)blockIdx.x / bpc; c < ncl; c += (int)gridDim.x / bpc) {
+        int64_t base = 0, end = sp.n;
+        if (sp.blk) {
+            if (sp.ctop[c] < level || sp.cstat[c]) continue;
+            base = sp.cbase[c];
+            end = sp.cend[c];
+        }
+        const int64_t lo = base + (((end - base - 1) >> level) << level);
+        if (lo + (1ll << (level - 1)) < end) continue;  // the last node has a right child
+        const int cnt = cs[lo];
+        for (int64_t e = part * (int64_t)blockDim.x + threadIdx.x; e < cnt; e += (int64_t)bpc * blockDim.x) {
+            Wd[2 * lo + e] = Ws[2 * lo + e];
+            Ad[2 * lo + e] = As[2 * lo + e];
+            Bd[2 * lo + e] = Bs[2 * lo + e];
+        }
+        if (part == 0 && threadIdx.x == 0) cd[lo] = cnt;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) (up ? p1.cnt[dst] : p0.cnt[dst])[lo] = c;
 }
 
-int launch_level(const Points &pts, int64_t n, int level, PassBufs *passes, int npass, int32_t *status,
+int launch_passthrough(const Span &sp, int ncl, int level, PassBufs *passes, int32_t *status, cudaStream_t st)
+{
+    if (!sp.blk) {  // one cloud: only when its last node has no right child
+        const int64_t lo = ((sp.n - 1) >> level) << level;
+        if (lo + (1ll << (level - 1)) < sp.n) return 0;
+        int64_t blocks = (2 * (sp.n - lo) + 255) / 256;
+        if (blocks > 1024) blocks = 1024;
+        k_passthrough<<<dim3((unsigned)blocks, 2), 256, 0, st>>>(sp, 1, (int)blocks, level, passes[0], passes[1],
+                                                                 status);
+        return 1;
+    }
+    const int g = ncl < 4096 ? ncl : 4096;
+    k_passthrough<<<dim3((unsigned)(g > 0 ? g : 1), 2), 256, 0, st>>>(sp, ncl, 1, level, passes[0], passes[1], status);
+    return 1;
+}
+
+int launch_level(const Points &pts, const Span &sp, int level, PassBufs *passes, int npass, int32_t *status,
                  cudaStream_t st, int occupancy, int max_events, const LevelOrder *ord, int ab_level)
 {
     int launches = 0;
-    int64_t nodes = (n + (1ll << level) - 1) >> level;
+    const int64_t nodes = (sp.n + (1ll << level) - 1) >> level;
     dim3 g((unsigned)((nodes + 127) / 128), npass);
     const uint32_t *order = nullptr;
     int64_t entries = 0;
     if (ord && npass == 2) {
         entries = 2 * nodes;
-        k_order_keys<<<(unsigned)((entries + 255) / 256), 256, 0, st>>>(n, level, passes[0], passes[1], nodes,
+        k_order_keys<<<(unsigned)((entries + 255) / 256), 256, 0, st>>>(sp, level, passes[0], passes[1], nodes,
                                                                          ord->k0, ord->v0);
         int64_t sl = 0;
         const int which = radix_sort_pairs(ord->k0, ord->v0, ord->k1, ord->v1, entries, nullptr, 16, ord->ss, st, &sl);
@@ -187,25 +222,12 @@ int launch_level(const Points &pts, int64_t n, int level, PassBufs *passes, int 
     const Points &P = pts;
     PassBufs &a = passes[0], &b = passes[npass - 1];
     const int ab = ab_level;
-    if (occupancy >= 4) k_level<4><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, order, entries, ab, status);
-    else if (occupancy == 3) k_level<3><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, order, entries, ab, status);
-    else if (occupancy == 2) k_level<2><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, order, entries, ab, status);
-    else k_level<1><<<g, 128, sm, st>>>(P, n, level, a, b, max_events, order, entries, ab, status);
+    if (occupancy >= 4) k_level<4><<<g, 128, sm, st>>>(P, sp, level, a, b, max_events, order, entries, ab, status);
+    else if (occupancy == 3) k_level<3><<<g, 128, sm, st>>>(P, sp, level, a, b, max_events, order, entries, ab, status);
+    else if (occupancy == 2) k_level<2><<<g, 128, sm, st>>>(P, sp, level, a, b, max_events, order, entries, ab, status);
+    else k_level<1><<<g, 128, sm, st>>>(P, sp, level, a, b, max_events, order, entries, ab, status);
     launches++;
-    int64_t lo = (nodes - 1) << level;
-    if (max_events < 0 && lo + (1ll << (level - 1)) >= n) {
-        launch_passthrough(n, level, lo, passes, status, st);
-        launches++;
-    }
     return launches;
-}
-
-void launch_passthrough(int64_t n, int level, int64_t lo, PassBufs *passes, int32_t *status, cudaStream_t st)
-{
-    int64_t cap = 2 * (n - lo);
-    unsigned blocks = (unsigned)((cap + 255) / 256);
-    if (blocks > 1024) blocks = 1024;
-    k_passthrough<<<dim3(blocks, 2), 256, 0, st>>>(lo, level, passes[0], passes[1], status);
 }
 
 // ---------------------------------------------------------------------------
@@ -241,7 +263,7 @@ constexpr int CMP_THREADS = 32;
 
 // Merges with more than max_events child events are left to the time-segment
 // kernels (max_events < 0: none).
-__global__ void __launch_bounds__(CMP_THREADS) k_level_cmp(Points pts, int64_t n, int level, PassBufs p0, PassBufs p1,
+__global__ void __launch_bounds__(CMP_THREADS) k_level_cmp(Points pts, Span sp, int level, PassBufs p0, PassBufs p1,
                                                            int scap, int max_events, int32_t *status)
 {
     extern __shared__ int sm[];
@@ -249,9 +271,10 @@ __global__ void __launch_bounds__(CMP_THREADS) k_level_cmp(Points pts, int64_t n
     if (*status) return;
     const bool upper = blockIdx.y != 0;
     const int64_t lo = (int64_t)blockIdx.x << level;
-    if (lo >= n) return;
+    int64_t hi;
+    if (!node_span(sp, level, lo, hi)) return;
     const int64_t half = 1ll << (level - 1);
-    const int64_t mid = lo + half, hi = (lo + 2 * half < n) ? lo + 2 * half : n;
+    const int64_t mid = lo + half;
     if (mid >= hi) return;  // pass-through nodes are copied by k_passthrough
     const int src = (level - 1) & 1, dst = level & 1;
     const int *csrc = upper ? p1.cnt[src] : p0.cnt[src];
@@ -359,15 +382,13 @@ __global__ void __launch_bounds__(CMP_THREADS) k_level_cmp(Points pts, int64_t n
 size_t cmp_smem_bytes(int scap) { return (size_t)scap * (sizeof(int4) + sizeof(int2) + 4 * sizeof(int)); }
 
 
-void launch_level_cmp(const Points &pts, int64_t n, int level, PassBufs *passes, int npass, int32_t *status,
+void launch_level_cmp(const Points &pts, const Span &sp, int level, PassBufs *passes, int npass, int32_t *status,
                       cudaStream_t st, int scap, int max_events)
 {
-    int64_t nodes = (n + (1ll << level) - 1) >> level;
+    const int64_t nodes = (sp.n + (1ll << level) - 1) >> level;
     dim3 g((unsigned)nodes, npass);
-    k_level_cmp<<<g, CMP_THREADS, cmp_smem_bytes(scap), st>>>(pts, n, level, passes[0], passes[npass - 1], scap,
+    k_level_cmp<<<g, CMP_THREADS, cmp_smem_bytes(scap), st>>>(pts, sp, level, passes[0], passes[npass - 1], scap,
                                                               max_events, status);
-    int64_t lo = (nodes - 1) << level;
-    if (max_events < 0 && lo + (1ll << (level - 1)) >= n) launch_passthrough(n, level, lo, passes, status, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -8,6 +8,7 @@ __device__ __forceinline__ void seg_status(int32_t *status, int code) { atomicCA
 
 struct SegArgs {
     Points pts;
+    Span sp;
     SegGeom geo;
     PassBufs pb[2];
     SegBufs sb[2];
@@ -34,8 +35,9 @@ __global__ void k_seg_bounds(SegArgs a)
     const int s = (int)(t % G.smax);
     const int64_t half = 1ll << (G.level - 1);
     const int64_t lo = m << G.level;
-    if (lo >= G.n) return;
-    const int64_t mid = lo + half, hi = (lo + 2 * half < G.n) ? lo + 2 * half : G.n;
+    int64_t hi;
+    if (!node_span(a.sp, G.level, lo, hi)) return;
+    const int64_t mid = lo + half;
     if (mid >= hi) return;
     const PassBufs &pb = a.pb[pass];
     const SegBufs &sb = a.sb[pass];
@@ -74,15 +76,17 @@ __global__ void k_seg_bounds(SegArgs a)
 
 // Maps a position q of the level's source movie buffer to its child movie:
 // returns false when q holds no event of a merged child.
-__device__ __forceinline__ bool seg_locate(const SegGeom &G, const PassBufs &pb, int64_t q, int64_t &clo, int64_t &plo,
-                                           int &k, int &E)
+__device__ __forceinline__ bool seg_locate(const Span &sp, const SegGeom &G, const PassBufs &pb, int64_t q,
+                                           int64_t &clo, int64_t &plo, int &k, int &E)
 {
     const int64_t half = 1ll << (G.level - 1);
     const int64_t r = q >> 1;
-    if (r >= G.n) return false;
+    if (r >= sp.n) return false;
     clo = r & ~(half - 1);
     plo = r & ~(2 * half - 1);
-    const int64_t pmid = plo + half, phi = (plo + 2 * half < G.n) ? plo + 2 * half : G.n;
+    const int64_t pmid = plo + half;
+    int64_t phi;
+    if (!node_span(sp, G.level, plo, phi)) return false;
     if (pmid >= phi) return false;  // pass-through node
     k = (int)(q - 2 * clo);
     E = pb.cnt[(G.level - 1) & 1][clo];
@@ -157,7 +161,7 @@ __device__ void seg_pairs_one(const SegArgs &a, int pass, int64_t q, bool valid)
     int64_t m = 0;
     const PassBufs &pb = a.pb[pass];
     const SegBufs &sb = a.sb[pass];
-    if (valid && seg_locate(G, pb, q, clo, plo, k, E)) {
+    if (valid && seg_locate(a.sp, G, pb, q, clo, plo, k, E)) {
         const unsigned *CW = pb.W[(G.level - 1) & 1] + 2 * clo;
         const unsigned w = CW[k];
         rk = (int)(w & RANK_MASK);
@@ -280,8 +284,9 @@ __device__ void seg_window(const SegArgs &a, int pass, int64_t g, int retry, int
     const int s = (int)(g % G.smax);
     const int64_t half = 1ll << (G.level - 1);
     const int64_t lo = m << G.level;
-    if (lo >= G.n) return;
-    const int64_t mid = lo + half, hi = (lo + 2 * half < G.n) ? lo + 2 * half : G.n;
+    int64_t hi;
+    if (!node_span(a.sp, G.level, lo, hi)) return;
+    const int64_t mid = lo + half;
     if (mid >= hi) return;
     const PassBufs &pb = a.pb[pass];
     const SegBufs &sb = a.sb[pass];
@@ -455,8 +460,9 @@ __device__ void seg_concat_one(const SegArgs &a, int pass, int64_t m)
     const SegGeom &G = a.geo;
     const int64_t half = 1ll << (G.level - 1);
     const int64_t lo = m << G.level;
-    if (lo >= G.n) return;
-    const int64_t mid = lo + half, hi = (lo + 2 * half < G.n) ? lo + 2 * half : G.n;
+    int64_t hi;
+    if (!node_span(a.sp, G.level, lo, hi)) return;
+    const int64_t mid = lo + half;
     if (mid >= hi) return;
     const PassBufs &pb = a.pb[pass];
     const SegBufs &sb = a.sb[pass];
@@ -517,8 +523,9 @@ __global__ void k_seg_fallback(SegArgs a)
     const int64_t m = (int64_t)(e & 0x7fffffffu);
     const int64_t half = 1ll << (G.level - 1);
     const int64_t lo = m << G.level;
-    if (lo >= G.n) return;
-    const int64_t mid = lo + half, hi = (lo + 2 * half < G.n) ? lo + 2 * half : G.n;
+    int64_t hi;
+    if (!node_span(a.sp, G.level, lo, hi)) return;
+    const int64_t mid = lo + half;
     if (mid >= hi) return;
     const PassBufs &pb = a.pb[pass];
     if (!a.sb[pass].nofit[m] || a.sb[pass].nseg[m] == 0) return;
@@ -542,13 +549,15 @@ void seg_kernel_attributes()
 
 size_t seg_smem_bytes(int scap, int K) { return (size_t)scap * (sizeof(int4) + sizeof(int2) + sizeof(int)) + 4 * (K + 1); }
 
-void launch_seg_level(const Points &pts, int64_t n, int level, PassBufs *passes, SegBufs *sbufs, uint64_t *pairs,
+void launch_seg_level(const Points &pts, const Span &sp, int level, PassBufs *passes, SegBufs *sbufs, uint64_t *pairs,
                       uint32_t *pair_vals, uint64_t *pairs_alt, uint32_t *vals_alt, unsigned long long *npairs,
                       int *overflow, int64_t pair_cap, int64_t S_cap, int64_t M_cap, int K, int Kmin, int scap,
                       int min_events, const SortScratch &ss, int32_t *status, cudaStream_t st, int64_t *launches)
 {
     SegArgs a;
     a.pts = pts;
+    a.sp = sp;
+    const int64_t n = sp.n;  // the rank space
     a.geo.n = n;
     a.geo.level = level;
     a.geo.K = K;
@@ -606,11 +615,6 @@ void launch_seg_level(const Points &pts, int64_t n, int level, PassBufs *passes,
     const int64_t fb_threads = 2 * M;
     k_seg_fallback<<<(unsigned)((fb_threads + 63) / 64), 64, 0, st>>>(a);
     *launches += 4;
-    const int64_t last_lo = (M - 1) << level;
-    if (last_lo + (1ll << (level - 1)) >= n) {
-        launch_passthrough(n, level, last_lo, passes, status, st);
-        *launches += 1;
-    }
 }
 
 }  // namespace hull3d

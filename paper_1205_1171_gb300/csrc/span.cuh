@@ -17,6 +17,7 @@ constexpr int SPAN_SHIFT = 13;  // clouds of the multi-cloud rank space hold mor
 struct Span {
     int64_t n;            // ranks in use: one cloud's n, or the end of the last block
     const int32_t *blk;   // nullptr: one cloud.  Else the cloud owning each 2^SPAN_SHIFT ranks (-1: none)
+    const int64_t *cbase; // per cloud: first rank of its block
     const int64_t *cend;  // per cloud: one past its last rank (block start + n_c)
     const int32_t *ctop;  // per cloud: its root level L_c
     const int32_t *cstat; // per cloud: nonzero once an input error was found (its nodes are skipped)
@@ -25,11 +26,11 @@ struct Span {
 // The node of `level` whose first rank is lo (a multiple of 2^level): false
 // when there is none there (past the ranks in use, in a cloud's padding,
 // above its cloud's root, or in a failed cloud); else hi = the node's end,
-// min(lo + 2^level, end of its cloud).
-__host__ __device__ __forceinline__ bool node_span(const Span &sp, int level, int64_t lo, int64_t &hi)
+// min(lo + 2^level, end), with end the end of its cloud.
+__host__ __device__ __forceinline__ bool node_span(const Span &sp, int level, int64_t lo, int64_t &hi, int64_t &end)
 {
     if (lo >= sp.n) return false;
-    int64_t end = sp.n;
+    end = sp.n;
     if (sp.blk) {
         const int32_t c = sp.blk[lo >> SPAN_SHIFT];
         if (c < 0 || sp.ctop[c] < level || sp.cstat[c]) return false;
@@ -39,5 +40,14 @@ __host__ __device__ __forceinline__ bool node_span(const Span &sp, int level, in
     hi = lo + (1ll << level) < end ? lo + (1ll << level) : end;
     return true;
 }
+
+__host__ __device__ __forceinline__ bool node_span(const Span &sp, int level, int64_t lo, int64_t &hi)
+{
+    int64_t end;
+    return node_span(sp, level, lo, hi, end);
+}
+
+// One cloud of n ranks.
+inline Span single_span(int64_t n) { return Span{ n, nullptr, nullptr, nullptr, nullptr, nullptr }; }
 
 }  // namespace hull3d

@@ -11,8 +11,10 @@ array.  One scheduler thread
     for the persistent batched kernel, double-buffered on two streams: a
     batch launches as soon as a batch slot is free, so requests that arrive
     while others run join the next batch (continuous batching);
-  * runs large clouds on a pool of resident plans, one CUDA stream each, so
-    several overlap on the device;
+  * gathers admitted large clouds the same way into batches for resident
+    large-cloud slots, each batch hulled together level by level (one launch
+    sequence per merge level for all its clouds), a batch taking requests
+    while their aligned rank blocks fit the slot's rank space;
   * polls completion events, copies results back, resolves futures and
     returns their bytes to the budget.
 All device buffers (plans, staging rings) are allocated once at start and
@@ -41,6 +43,12 @@ class ServeError(RuntimeError):
 def footprint(n: int) -> int:
     """Device bytes a request holds while in flight (its input and output rows)."""
     return 12 * n + 12 * max(2 * n - 4, 1)
+
+
+def rank_block(n: int) -> int:
+    """Ranks a cloud takes in a large-cloud batch: its aligned block, the
+    smallest power of two >= n."""
+    return 1 << max(0, int(n) - 1).bit_length()
 
 
 @dataclass
@@ -77,46 +85,41 @@ class Stats:
 
 
 class CudaBackend:
-    """GPU work through the C ABI: batch slots and a pool of large-cloud plans."""
+    """GPU work through the C ABI: double-buffered batch slots for small
+    clouds (the one-CTA batch kernel) and for large clouds (hulled together,
+    level by level), each slot with its own plan, stream and resident
+    device and pinned host buffers."""
 
     def __init__(self, small_max: int = 4096, batch_points: int = 1 << 21, batch_clouds: int = 8192,
-                 large_slots: int = 8, large_max: int = 1 << 18, device: str = "cuda"):
+                 large_slots: int = 2, large_max: int = 1 << 18, large_rank_space: int = 1 << 21,
+                 large_clouds: int = 1024, device: str = "cuda"):
         import torch
 
         from paper_1205_1171_gb300 import hull3d
 
         self.torch, self.H = torch, hull3d
         self.small_max, self.batch_points, self.batch_clouds = small_max, batch_points, batch_clouds
-        self.large_max = large_max
+        self.large_max, self.large_rank_space, self.large_clouds = large_max, large_rank_space, large_clouds
+        if rank_block(large_max) > large_rank_space:
+            raise ValueError("the largest request must fit a large slot's rank space")
         dev = torch.device(device)
-        self.batch_slots = []
-        for _ in range(2):
-            self.batch_slots.append({
-                "plan": hull3d.Hull3D(small_max, max_clouds=batch_clouds),
-                "stream": torch.cuda.Stream(dev),
-                "xyz": torch.empty((batch_points, 3), dtype=torch.int32, device=dev),
-                "faces": torch.empty((2 * batch_points, 3), dtype=torch.int32, device=dev),
-                "nf": torch.zeros(batch_clouds, dtype=torch.int64, device=dev),
-                "st": torch.zeros(batch_clouds, dtype=torch.int32, device=dev),
-                "h_xyz": torch.empty((batch_points, 3), dtype=torch.int32).pin_memory(),
-                "h_faces": torch.empty((2 * batch_points, 3), dtype=torch.int32).pin_memory(),
-                "h_nf": torch.zeros(batch_clouds, dtype=torch.int64).pin_memory(),
-                "h_st": torch.zeros(batch_clouds, dtype=torch.int32).pin_memory(),
-                "busy": None})
-        self.large_slots = []
-        for _ in range(large_slots):
-            self.large_slots.append({
-                "plan": hull3d.Hull3D(large_max, use_graph=-1),  # sizes vary: no graph re-capture per request
-                "stream": torch.cuda.Stream(dev),
-                "xyz": torch.empty((large_max, 3), dtype=torch.int32, device=dev),
-                "faces": torch.empty((2 * large_max, 3), dtype=torch.int32, device=dev),
-                "nf": torch.zeros(1, dtype=torch.int64, device=dev),
-                "st": torch.zeros(1, dtype=torch.int32, device=dev),
-                "h_xyz": torch.empty((large_max, 3), dtype=torch.int32).pin_memory(),
-                "h_faces": torch.empty((2 * large_max, 3), dtype=torch.int32).pin_memory(),
-                "h_nf": torch.zeros(1, dtype=torch.int64).pin_memory(),
-                "h_st": torch.zeros(1, dtype=torch.int32).pin_memory(),
-                "busy": None})
+
+        def slot(max_n, points, clouds):
+            return {"plan": hull3d.Hull3D(max_n, max_clouds=clouds),
+                    "stream": torch.cuda.Stream(dev),
+                    "xyz": torch.empty((points, 3), dtype=torch.int32, device=dev),
+                    "faces": torch.empty((2 * points, 3), dtype=torch.int32, device=dev),
+                    "nf": torch.zeros(clouds, dtype=torch.int64, device=dev),
+                    "st": torch.zeros(clouds, dtype=torch.int32, device=dev),
+                    "h_xyz": torch.empty((points, 3), dtype=torch.int32).pin_memory(),
+                    "h_faces": torch.empty((2 * points, 3), dtype=torch.int32).pin_memory(),
+                    "h_nf": torch.zeros(clouds, dtype=torch.int64).pin_memory(),
+                    "h_st": torch.zeros(clouds, dtype=torch.int32).pin_memory(),
+                    "busy": None}
+
+        self.batch_slots = [slot(small_max, batch_points, batch_clouds) for _ in range(2)]
+        # a large batch holds at most large_rank_space points (their blocks fill that many ranks)
+        self.large_slots = [slot(large_rank_space, large_rank_space, large_clouds) for _ in range(large_slots)]
 
     def resident_bytes(self) -> int:
         b = 0
@@ -124,32 +127,7 @@ class CudaBackend:
             b += s["plan"].scratch_bytes + s["xyz"].numel() * 4 + s["faces"].numel() * 4
         return b
 
-    # -- large clouds -------------------------------------------------------
-    def free_large(self):
-        return [s for s in self.large_slots if s["busy"] is None]
-
-    def launch_large(self, slot, req: Request):
-        torch = self.torch
-        n = req.n
-        with torch.cuda.stream(slot["stream"]):
-            slot["h_xyz"][:n].numpy()[:] = req.points
-            slot["xyz"][:n].copy_(slot["h_xyz"][:n], non_blocking=True)
-            cap = max(2 * n - 4, 1)
-            slot["plan"].compute_async(slot["xyz"][:n], slot["faces"][:cap], slot["nf"], slot["st"], slot["stream"])
-            # results to pinned host memory on the same stream: completion
-            # then needs no device call from the scheduler thread
-            slot["h_nf"].copy_(slot["nf"], non_blocking=True)
-            slot["h_st"].copy_(slot["st"], non_blocking=True)
-            slot["h_faces"][:cap].copy_(slot["faces"][:cap], non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(slot["stream"])
-        slot["busy"] = (ev, [req])
-
-    # -- batches --------------------------------------------------------------
-    def free_batch(self):
-        return [s for s in self.batch_slots if s["busy"] is None]
-
-    def launch_batch(self, slot, reqs: list):
+    def _launch(self, slot, reqs: list):
         torch = self.torch
         sizes = np.array([r.n for r in reqs], np.int64)
         off = np.zeros(len(reqs) + 1, np.int64)
@@ -164,6 +142,8 @@ class CudaBackend:
         with torch.cuda.stream(slot["stream"]):
             slot["xyz"][:N].copy_(slot["h_xyz"][:N], non_blocking=True)
             slot["plan"].batch_async(slot["xyz"], off, slot["faces"], foff, slot["nf"], slot["st"], slot["stream"])
+            # results to pinned host memory on the same stream: completion
+            # then needs no device call from the scheduler thread
             F = int(foff[-1])
             if F:
                 slot["h_faces"][:F].copy_(slot["faces"][:F], non_blocking=True)
@@ -174,21 +154,25 @@ class CudaBackend:
             ev.record(slot["stream"])
         slot["busy"] = (ev, reqs, foff)
 
+    # -- large clouds -------------------------------------------------------
+    def free_large(self):
+        return [s for s in self.large_slots if s["busy"] is None]
+
+    def launch_large(self, slot, reqs: list):
+        self._launch(slot, reqs)
+
+    # -- small clouds ---------------------------------------------------------
+    def free_batch(self):
+        return [s for s in self.batch_slots if s["busy"] is None]
+
+    def launch_batch(self, slot, reqs: list):
+        self._launch(slot, reqs)
+
     # -- completion -----------------------------------------------------------
     def poll(self):
         """Completed work as (request, faces or exception) pairs; frees the slots."""
         out = []
-        for slot in self.large_slots:
-            if slot["busy"] is not None and slot["busy"][0].query():
-                _, reqs = slot["busy"]
-                st = int(slot["h_st"][0])
-                if st:
-                    out.append((reqs[0], self.H.Hull3DError(st, "serve")))
-                else:
-                    nf = int(slot["h_nf"][0])
-                    out.append((reqs[0], slot["h_faces"][:nf].numpy().copy()))
-                slot["busy"] = None
-        for slot in self.batch_slots:
+        for slot in self.batch_slots + self.large_slots:
             if slot["busy"] is not None and slot["busy"][0].query():
                 _, reqs, foff = slot["busy"]
                 B = len(reqs)
@@ -284,13 +268,21 @@ class HullServer:
         return self.inflight + footprint(n) <= self.budget - self.resident
 
     def _dispatch(self):
-        # large clouds: every free plan slot, in arrival order, while memory allows
+        # large clouds: a free large slot takes everything pending, in arrival
+        # order, while memory allows and their rank blocks fit its rank space
+        space_cap = getattr(self.backend, "large_rank_space", 1 << 62)
+        count_cap = getattr(self.backend, "large_clouds", 1 << 30)
         for slot in self.backend.free_large():
-            if not self._large or not self._fits(self._large[0].n):
+            batch, space = [], 0
+            while (self._large and len(batch) < count_cap and space + rank_block(self._large[0].n) <= space_cap
+                   and self._fits(self._large[0].n)):
+                r = self._large.popleft()
+                self.inflight += footprint(r.n)
+                space += rank_block(r.n)
+                batch.append(r)
+            if not batch:
                 break
-            r = self._large.popleft()
-            self.inflight += footprint(r.n)
-            self.backend.launch_large(slot, r)
+            self.backend.launch_large(slot, batch)
             self.stats.large += 1
         # small clouds: a free batch slot takes everything pending that fits
         free = self.backend.free_batch()

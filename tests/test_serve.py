@@ -12,8 +12,9 @@ from paper_1205_1171_gb300 import inputs, serve
 class FakeBackend:
     """Completes work after a fixed delay; records what ran together."""
 
-    def __init__(self, delay=0.002, resident=1000, large_slots=2, large_max=1 << 20):
+    def __init__(self, delay=0.002, resident=1000, large_slots=2, large_max=1 << 20, large_rank_space=1 << 22):
         self.delay, self.res, self.large_max = delay, resident, large_max
+        self.large_rank_space = large_rank_space
         self.large = [None] * large_slots
         self.batches = [None, None]
         self.log = []
@@ -24,9 +25,9 @@ class FakeBackend:
     def free_large(self):
         return [i for i, s in enumerate(self.large) if s is None]
 
-    def launch_large(self, slot, req):
-        self.large[slot] = (time.perf_counter() + self.delay, [req])
-        self.log.append(("large", [req.rid]))
+    def launch_large(self, slot, reqs):
+        self.large[slot] = (time.perf_counter() + self.delay, reqs)
+        self.log.append(("large", [r.rid for r in reqs]))
 
     def free_batch(self):
         return [i for i, s in enumerate(self.batches) if s is None]
@@ -89,6 +90,19 @@ def test_requests_arriving_during_a_batch_join_the_next_one():
     assert len(batches) >= 2 and sum(len(b) for b in batches) == 8
 
 
+def test_large_requests_are_batched_within_the_rank_space():
+    # rank space 2^16: blocks of 2^14 (9000 points) fit four to a batch
+    fb = FakeBackend(delay=0.05, large_slots=1, large_rank_space=1 << 16)
+    with serve.HullServer(fb, budget_bytes=1 << 30, small_max=4096) as srv:
+        futs = [srv.submit(np.zeros((9000, 3), np.int32)) for _ in range(10)]
+        for f in futs:
+            f.result(timeout=10)
+    larges = [ids for k, ids in fb.log if k == "large"]
+    assert sum(len(b) for b in larges) == 10
+    assert max(len(b) for b in larges) <= 4 and max(len(b) for b in larges) >= 2
+    assert serve.rank_block(9000) == 1 << 14 and serve.rank_block(8192) == 8192 and serve.rank_block(1) == 1
+
+
 def test_poisson_arrivals_have_the_requested_rate():
     t = serve.poisson_arrivals(20000.0, 1.0, np.random.default_rng(1))
     assert 19000 < len(t) < 21000 and np.all(np.diff(t) > 0) and t[-1] < 1.0
@@ -106,7 +120,8 @@ def test_results_identical_alone_and_in_the_mix():
     dup = inputs.cloud_seeded("ball", 100, 3).copy()
     dup[7] = dup[3]
     pool.append(dup)
-    backend = serve.CudaBackend(batch_points=1 << 18, batch_clouds=256, large_slots=3, large_max=1 << 16)
+    backend = serve.CudaBackend(batch_points=1 << 18, batch_clouds=256, large_slots=2, large_max=1 << 16,
+                                large_rank_space=1 << 18, large_clouds=64)
     single = hull3d.Hull3D(1 << 16)
     try:
         with serve.HullServer(backend, budget_bytes=4 << 30) as srv:
