@@ -57,11 +57,12 @@ def _load():
             lib.oracle_sort_order.argtypes = [P, i64, P]
             lib.oracle_node_events.argtypes = [P, i64, i64, i64, ctypes.c_int, P, P, P, P, i64, P, P, P]
             lib.oracle_brute_faces.argtypes = [P, i64, P, i64, P]
+            lib.oracle_delaunay.argtypes = [P, i64, P, i64, P]
             lib.oracle_turn_sign.argtypes = [P, P]
             lib.oracle_time_cmp.argtypes = [P, P]
             lib.oracle_orient3d_sign.argtypes = [P, P]
             for f in (lib.oracle_hull, lib.oracle_sort_order, lib.oracle_node_events, lib.oracle_brute_faces,
-                      lib.oracle_turn_sign, lib.oracle_time_cmp, lib.oracle_orient3d_sign):
+                      lib.oracle_turn_sign, lib.oracle_time_cmp, lib.oracle_orient3d_sign, lib.oracle_delaunay):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -91,6 +92,25 @@ def hull(xyz, split: str = "half") -> np.ndarray:
     if rc:
         raise OracleError(rc, "hull")
     return faces[: nf.value].copy()
+
+
+def delaunay(xy) -> np.ndarray:
+    """Canonical triangle list (T x 3 int32) of the 2D Delaunay triangulation
+    of the (n, 2) int32 points (|x|, |y| < 2^15) through the lifting map: the
+    lower hull of (x, y, x^2 + y^2) by the method's lower pass, triangles
+    counter-clockwise in the plane, rotated min-first, sorted."""
+    lib = _load()
+    a = np.ascontiguousarray(np.asarray(xy), dtype=np.int32)
+    if a.ndim != 2 or a.shape[1] != 2:
+        raise ValueError("points must be an (n, 2) array")
+    n = a.shape[0]
+    cap = max(2 * n, 2)
+    tris = np.zeros((cap, 3), dtype=np.int32)
+    nt = ctypes.c_int64(0)
+    rc = lib.oracle_delaunay(_ptr(a), n, _ptr(tris), cap, ctypes.byref(nt))
+    if rc:
+        raise OracleError(rc, "delaunay")
+    return tris[: nt.value].copy()
 
 
 def sort_order(xyz) -> np.ndarray:

@@ -659,6 +659,77 @@ int oracle_brute_faces(const int32_t *xyz, int64_t n, int32_t *faces, int64_t ca
     return OK;
 }
 
+/* ------------------------------------------------------------------------ */
+/* 2D Delaunay triangulation through the lifting map.                         */
+/* ------------------------------------------------------------------------ */
+/* The points (x, y) lifted to (x, y, x^2 + y^2) lie on a paraboloid; a triple
+ * is a lower face of their 3D hull exactly when no other point lies inside
+ * the triple's circumcircle, so the lower hull projects to the Delaunay
+ * triangulation.  Here the lower pass of the method above (Sec. 2) runs on
+ * the lifted points, with the same perturbation (so four cocircular points
+ * get one consistent diagonal).  Coordinates are limited to |x|, |y| < 2^15:
+ * the lifted z < 2^31, coordinate differences < 2^31, 2D cross products of
+ * the (x, z) and (x, y) projections < 2^48 (int64), their products < 2^97
+ * (__int128), orient3d < 2^66 -- the widths of the 3D hull above still hold.
+ * A lower face whose three points are collinear in the plane (points on one
+ * edge of the convex hull, which the perturbation may turn into a sliver) has
+ * zero area and is not a triangle of the triangulation: it is left out.  The
+ * triangles are written counter-clockwise in the plane, rotated min-first and
+ * sorted. */
+#define LIFT_LIM ((1 << 15) - 1)
+
+int oracle_delaunay(const int32_t *xy, int64_t n, int32_t *tris, int64_t cap, int64_t *ntris)
+{
+    if (!ntris) return E_INVALID;
+    *ntris = 0;
+    if (n < 1 || !xy) return E_INVALID;
+    Pt *P = (Pt *)malloc(sizeof(Pt) * (size_t)n);
+    if (!P) return E_NOMEM;
+    for (int64_t i = 0; i < n; i++) {
+        const int64_t x = xy[2 * i], y = xy[2 * i + 1];
+        if (x < -LIFT_LIM || x > LIFT_LIM || y < -LIFT_LIM || y > LIFT_LIM) { free(P); return E_RANGE; }
+        P[i] = (Pt){ x, y, x * x + y * y, (int)i };
+    }
+    qsort(P, (size_t)n, sizeof(Pt), qsort_pt);
+    for (int64_t i = 1; i < n; i++)
+        if (xcmp_pt(&P[i - 1], &P[i]) == 0) { free(P); return E_DUP; }
+    if (n < 3) { free(P); return OK; }
+    int32_t *prv = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *nxt = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    Ev *A = (Ev *)malloc(sizeof(Ev) * (size_t)(2 * n));
+    Ev *B = (Ev *)malloc(sizeof(Ev) * (size_t)(2 * n));
+    int32_t *tmp = (int32_t *)malloc(sizeof(int32_t) * 3 * (size_t)(2 * n));
+    if (!prv || !nxt || !A || !B || !tmp) {
+        free(P); free(prv); free(nxt); free(A); free(B); free(tmp);
+        return E_NOMEM;
+    }
+    Ctx c = { P, prv, nxt, 0, 0 };
+    int64_t k = movie(&c, 0, n, A, B); /* the lower pass only */
+    int rc = OK;
+    int64_t nt = 0;
+    for (int64_t e = 0; e < k; e++) { /* replay the root movie: one face per event */
+        int32_t w = A[e].w, p = c.prv[w], r = c.nxt[w];
+        if (p != A[e].a || r != A[e].b) rc = E_INVALID;
+        const int64_t area = (P[w].x - P[p].x) * (P[r].y - P[p].y) - (P[r].x - P[p].x) * (P[w].y - P[p].y);
+        if (area != 0) {
+            int32_t f[3];
+            /* counter-clockwise in the plane */
+            if (area > 0) { f[0] = P[p].id; f[1] = P[w].id; f[2] = P[r].id; }
+            else { f[0] = P[p].id; f[1] = P[r].id; f[2] = P[w].id; }
+            canon_face(f);
+            memcpy(tmp + 3 * nt, f, sizeof f);
+            nt++;
+        }
+        act(&c, w);
+    }
+    qsort(tmp, (size_t)nt, 3 * sizeof(int32_t), qsort_face);
+    if (!rc && nt > cap) rc = E_CAP;
+    else if (!rc) memcpy(tris, tmp, sizeof(int32_t) * 3 * (size_t)nt);
+    *ntris = nt;
+    free(P); free(prv); free(nxt); free(A); free(B); free(tmp);
+    return rc;
+}
+
 /* Predicates on explicit points, for the predicate tests.  pts: k x 3 int32,
  * ids: k input indices (they pick the gam/eta infinitesimals). */
 int oracle_turn_sign(const int32_t *pts, const int32_t *ids)
