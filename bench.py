@@ -324,12 +324,27 @@ def batch_parity(faces, nf, foff, digests) -> dict:
     return {"clouds": len(digests), "bit_exact": True}
 
 
-def batched_leg(hull3d, torch, steps: int, cpu_baseline: bool = False):
+def batched_leg(hull3d, torch, steps: int, cpu_baseline: bool = False, clouds: int = 0):
     """65,536 independent clouds, sizes round(2^U(4, 12)), distribution drawn
-    per cloud: one persistent launch per size class vs per-cloud plain launches."""
+    per cloud: one persistent launch per size class vs per-cloud plain launches.
+    clouds > 0 (profiling runs only): that many clouds of the same draw, once."""
     from paper_1205_1171_gb300 import inputs
 
     xyz, off, kinds = inputs.batch(BATCH_CLOUDS, inputs.seed_for(4))
+    if clouds:
+        d_xyz = torch.from_numpy(xyz[: off[clouds]]).cuda()
+        sizes = np.diff(off[: clouds + 1])
+        foff = np.zeros(clouds + 1, np.int64)
+        foff[1:] = np.cumsum(np.where(sizes >= 3, 2 * sizes - 4, 0))
+        plan = hull3d.Hull3D(4096, max_clouds=clouds)
+        faces = torch.empty((int(foff[-1]), 3), dtype=torch.int32, device="cuda")
+        nf = torch.zeros(clouds, dtype=torch.int64, device="cuda")
+        st = torch.zeros(clouds, dtype=torch.int32, device="cuda")
+        plan.batch_async(d_xyz, off[: clouds + 1], faces, foff, nf, st, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        assert int((st != 0).sum().item()) == 0
+        plan.close()
+        return None
     sizes = np.diff(off)
     caps = np.where(sizes >= 3, 2 * sizes - 4, 0)
     foff = np.zeros(len(off), np.int64)
@@ -338,7 +353,7 @@ def batched_leg(hull3d, torch, steps: int, cpu_baseline: bool = False):
     faces = torch.empty((int(foff[-1]), 3), dtype=torch.int32, device="cuda")
     nf = torch.zeros(BATCH_CLOUDS, dtype=torch.int64, device="cuda")
     st = torch.zeros(BATCH_CLOUDS, dtype=torch.int32, device="cuda")
-    plan = hull3d.Hull3D(4096, max_clouds=BATCH_CLOUDS)
+    plan = hull3d.Hull3D.tuned(4096, max_clouds=BATCH_CLOUDS, kind="batch")
     stream = torch.cuda.current_stream()
     plan.batch_async(d_xyz, off, faces, foff, nf, st, stream)
     torch.cuda.synchronize()
@@ -351,6 +366,20 @@ def batched_leg(hull3d, torch, steps: int, cpu_baseline: bool = False):
     torch.cuda.synchronize()
     batch_ms = e0.elapsed_time(e1) / steps
     launches = plan.last_launches
+    batch_tune = {"knobs": plan.tuned_knobs,
+                  "source": "autotuner cache" if plan.tuned_knobs else "library defaults"}
+    if plan.tuned_knobs:  # the library defaults on the same batch, for comparison
+        dplan = hull3d.Hull3D(4096, max_clouds=BATCH_CLOUDS)
+        dplan.batch_async(d_xyz, off, faces, foff, nf, st, stream)
+        e0.record(stream)
+        for _ in range(steps):
+            dplan.batch_async(d_xyz, off, faces, foff, nf, st, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        batch_tune["default_hulls_per_s"] = BATCH_CLOUDS / (e0.elapsed_time(e1) / steps / 1e3)
+        dplan.close()
+        plan.batch_async(d_xyz, off, faces, foff, nf, st, stream)  # the tuned plan's faces are the ones checked
+        torch.cuda.synchronize()
     # per-cloud plain launches on a sample (a rate, so a sample measures it)
     single = hull3d.Hull3D(4096, use_graph=-1)
     pick = np.random.default_rng(0).choice(BATCH_CLOUDS, size=PLAIN_SAMPLE, replace=False)
@@ -377,11 +406,141 @@ def batched_leg(hull3d, torch, steps: int, cpu_baseline: bool = False):
     out = {"workload": "65,536 clouds, sizes round(2^U(4,12)) (16..4096), distribution per cloud uniform over "
                        "cube/ball/sphere/gauss", "points": int(len(xyz)), "roofline": roof,
            "hulls_per_s": BATCH_CLOUDS / (batch_ms / 1e3), "ms_per_batch": batch_ms, "launches_per_batch": launches,
+           "autotune": batch_tune,
            "per_cloud_plain_hulls_per_s": PLAIN_SAMPLE / (plain_ms / 1e3),
            "per_cloud_plain_sample": PLAIN_SAMPLE}
     if cpu_baseline:
         out["cpu_baseline"], digests = batched_cpu_baseline(xyz, off)
         out["parity"] = batch_parity(faces, nf, foff, digests)
+    return out
+
+
+def _cloud_mismatch(fa, na, fb, nb, foff):
+    """Per cloud: True where the two face lists (rows foff[b] ..) differ."""
+    rows = np.zeros(len(fa), bool)
+    rows[:] = (fa != fb).any(axis=1)
+    B = len(na)
+    wrong = na != nb
+    for b in np.flatnonzero(~wrong):
+        k = int(na[b])
+        if k and rows[foff[b]: foff[b] + k].any():
+            wrong[b] = True
+    return wrong
+
+
+def float32_ablation_leg(hull3d, torch):
+    """The paper's float32 arithmetic (Sec. 3, cl_float coordinates) against
+    the exact predicates, on the batch kernel: the fraction of clouds whose
+    faces differ from the exact faces (themselves checked against the oracle
+    in the tests and the batched leg), or that fail, on the 65,536-cloud batch
+    and on 1,024 seeded 4096-point cubes."""
+    from paper_1205_1171_gb300 import inputs
+
+    out = {"arith": "float32 coordinates, cross products, quotient times and comparisons (no perturbation)",
+           "kernel": "k_batch (clouds of at most 4096 points)"}
+    cases = {"batch_65536": inputs.batch(BATCH_CLOUDS, inputs.seed_for(4))}
+    cubes = [inputs.cloud_seeded("cube", 4096, inputs.seed_for(1) + 7919 * i) for i in range(1024)]
+    off = np.arange(0, 4096 * 1025, 4096, dtype=np.int64)
+    cases["cube4096_x1024"] = (np.concatenate(cubes), off, ["cube"] * 1024)
+    for name, (xyz, off, kinds) in cases.items():
+        B = len(off) - 1
+        sizes = np.diff(off)
+        foff = np.zeros(B + 1, np.int64)
+        foff[1:] = np.cumsum(np.where(sizes >= 3, 2 * sizes - 4, 0))
+        d_xyz = torch.from_numpy(xyz).cuda()
+        res = []
+        for f32 in (0, 1):
+            plan = hull3d.Hull3D(4096, max_clouds=B, float32_ablation=f32)
+            faces = torch.full((int(foff[-1]), 3), -1, dtype=torch.int32, device="cuda")
+            nf = torch.zeros(B, dtype=torch.int64, device="cuda")
+            st = torch.zeros(B, dtype=torch.int32, device="cuda")
+            plan.batch_async(d_xyz, off, faces, foff, nf, st)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            plan.batch_async(d_xyz, off, faces, foff, nf, st)
+            e1.record()
+            torch.cuda.synchronize()
+            res.append((faces.cpu().numpy(), nf.cpu().numpy(), st.cpu().numpy(), e0.elapsed_time(e1)))
+            plan.close()
+        (fe, ne, se, me), (ff, nff, sf, mf) = res
+        assert not se.any(), "exact batch failed"
+        failed = sf != 0
+        wrong = _cloud_mismatch(fe, ne, ff, nff, foff) & ~failed
+        rec = {"clouds": B, "wrong": int(wrong.sum()), "failed": int(failed.sum()),
+               "wrong_or_failed_frac": float((wrong | failed).mean()),
+               "exact_hulls_per_s": B / (me / 1e3), "float32_hulls_per_s": B / (mf / 1e3)}
+        kinds = np.array(kinds)
+        rec["by_dist"] = {d: float((wrong | failed)[kinds == d].mean()) for d in sorted(set(kinds.tolist()))}
+        cls = np.digitize(sizes, [257, 1025, 2049])
+        rec["by_size_class"] = {lab: float((wrong | failed)[cls == c].mean()) for c, lab in
+                                enumerate(("16-256", "257-1024", "1025-2048", "2049-4096")) if (cls == c).any()}
+        out[name] = rec
+    return out
+
+
+def _time_ms(torch, fn, reps: int, stream) -> float:
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def adjacency_leg(hull3d, torch, plan, faces, nfs, n_points, stream, reps: int = 5):
+    """Face neighbours and vertex stars (hull3d_adjacency_async) of the main
+    leg's hulls and of a 2^20-point sphere's (about 2.1 million faces)."""
+    from paper_1205_1171_gb300 import inputs
+
+    peak, peak_kind = peaks()
+    out = {}
+
+    def one(p, f, nf, n, label):
+        F = f.shape[0]
+        nb = torch.empty((F, 3), dtype=torch.int32, device="cuda")
+        off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+        star = torch.empty(3 * F, dtype=torch.int32, device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        ms = _time_ms(torch, lambda: p.adjacency_async(f, nf, n, nb, off, star, st, stream), reps, stream)
+        assert int(st.item()) == 0, "adjacency status"
+        faces_n = int(nf.item())
+        alg = 12 * faces_n + 12 * faces_n + 8 * (n + 1) + 12 * faces_n  # faces in; neighbours, offsets, stars out
+        out[label] = {"faces": faces_n, "ms": ms, "alg_bytes": alg, "gbs": alg / (ms / 1e3) / 1e9,
+                      "frac_of_hbm": alg / (ms / 1e3) / 1e9 / peak, "launches": p.last_launches}
+
+    for k, (f, nf) in enumerate(zip(faces, nfs)):
+        one(plan, f, nf, n_points, f"hull_2e24_{k}")
+    sph = torch.from_numpy(inputs.cloud_seeded("sphere", 1 << 20, inputs.seed_for(2))).cuda()
+    sp = hull3d.Hull3D(1 << 20)
+    fs = sp.compute(sph)
+    one(sp, fs, torch.tensor([fs.shape[0]], dtype=torch.int64, device="cuda"), 1 << 20, "sphere_2e20")
+    sp.close()
+    out["peak"] = peak
+    out["peak_kind"] = peak_kind
+    return out
+
+
+def delaunay_leg(hull3d, torch, stream):
+    """2D Delaunay triangulation through the lifting map (hull3d_delaunay_async)
+    of 2^20 and 2^22 points uniform in a disk."""
+    from paper_1205_1171_gb300 import inputs
+
+    out = {"input": "points uniform in the disk of radius 2^15 - 1 (int32), seed_for(60)"}
+    for n in (1 << 20, 1 << 22):
+        pts = torch.from_numpy(inputs.planar_seeded("disk", n, inputs.seed_for(60))).cuda()
+        p = hull3d.Hull3D(n)
+        tris = torch.empty((2 * n, 3), dtype=torch.int32, device="cuda")
+        nt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        ms = _time_ms(torch, lambda: p.delaunay_async(pts, tris, nt, st, stream), 3, stream)
+        assert int(st.item()) == 0, "delaunay status"
+        out[f"n_{n}"] = {"ms": ms, "mpoints_per_s": n / ms / 1e3, "triangles": int(nt.item()),
+                         "launches": p.last_launches}
+        p.close()
     return out
 
 
@@ -408,6 +567,7 @@ def serving_leg(hull3d, torch):
         for f in futs:
             f.result()
         served = srv.stats.summary()
+        srv_knobs = srv.backend.knobs
     plan = hull3d.Hull3D(1 << 18)
     lat = []
     host = [torch.from_numpy(pool[k]).pin_memory() for k in range(len(pool))]
@@ -432,7 +592,7 @@ def serving_leg(hull3d, torch):
                          "offered load is above what one GPU hulls, so a longer window only lengthens the backlog "
                          "(and the one-at-a-time replay of 200k requests would take minutes); both forms get the "
                          "same arrivals",
-            "served": served,
+            "served": served, "served_knobs": srv_knobs,
             "one_at_a_time": {"requests": int(len(lat)), "p50_ms": float(np.percentile(lat, 50)),
                               "p99_ms": float(np.percentile(lat, 99)), "hulls_per_s": len(lat) / span},
             "mean_points_per_request": pts}
@@ -460,6 +620,12 @@ def main():
     ap.add_argument("--seg-events", type=int, default=0, help="child events per time window (0 = default)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 65,536-cloud batched measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-ablation", action="store_true", help="skip the float32 arithmetic ablation")
+    ap.add_argument("--no-extras", action="store_true", help="skip the adjacency and Delaunay timings")
+    ap.add_argument("--profile-once", action="store_true",
+                    help="profiling runs only: hull each cloud once (no warm-up, no timing) and exit")
+    ap.add_argument("--batch-only", type=int, default=0,
+                    help="profiling runs only: run the batched leg on this many clouds once and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     npts = args.n
@@ -482,16 +648,31 @@ def main():
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
+    if args.batch_only:
+        batched_leg(hull3d, torch, 1, clouds=args.batch_only)
+        return
     dists = tuple(args.dists.split(","))
     clouds = make_inputs(rank, npts, dists)
     dev_clouds = [torch.from_numpy(c).cuda() for c in clouds]
-    plan = hull3d.Hull3D(npts, fused_levels=args.fused, level_occupancy=args.occ, cmp_level=args.cmp_level,
-                         seg_level=args.seg_level, seg_events=args.seg_events)
+    cli_knobs = dict(fused_levels=args.fused, level_occupancy=args.occ, cmp_level=args.cmp_level,
+                     seg_level=args.seg_level, seg_events=args.seg_events)
+    default_plan = not any(cli_knobs.values())
+    # the plan a user gets from Hull3D.tuned (the autotuner's knobs for this
+    # GPU, size and distribution class; the library defaults where none)
+    plan = hull3d.Hull3D.tuned(npts, dist_class="volume") if default_plan else hull3d.Hull3D(npts, **cli_knobs)
+    tuned_knobs = getattr(plan, "tuned_knobs", {}) if default_plan else {}
     cap = 2 * npts - 4
     faces = [torch.empty((cap, 3), dtype=torch.int32, device="cuda") for _ in clouds]
     nfs = [torch.zeros(1, dtype=torch.int64, device="cuda") for _ in clouds]
     sts = [torch.zeros(1, dtype=torch.int32, device="cuda") for _ in clouds]
     stream = torch.cuda.current_stream()
+    if args.profile_once:
+        for x, f, nf, st in zip(dev_clouds, faces, nfs, sts):
+            plan.compute_async(x, f, nf, st, stream)
+        torch.cuda.synchronize()
+        assert all(int(st.item()) == 0 for st in sts), "device status"
+        plan.close()
+        return
 
     def step():
         launches = 0
@@ -575,16 +756,17 @@ def main():
     o = plan.opts
     steps = max(args.steps, 1)
     L = int(np.ceil(np.log2(npts)))
-    klev = [lv for lv in range(plan.fused_levels_used + 1, L + 1) if lv < o["cmp_level"]]
+    # k_level runs from level 3 (level 2 has its own kernel) below the compacted levels
+    klev = [lv for lv in range(max(3, plan.fused_levels_used + 1), L + 1) if lv < o["cmp_level"]]
     k_bytes = sum(level_alg_bytes(npts, ev, lv) for ev in level_ev for lv in klev)  # per step
     k_ms = sum(float(level_ms[lv]) for lv in klev) / steps
     k_launches = len(klev) * len(clouds)
     achieved = k_bytes / (k_ms / 1e3) / 1e9 if k_ms > 0 else 0.0
     ab = [alg_bytes(npts, ev, plan.fused_levels_used, nf, o["seg_level"]) for ev, nf in zip(level_ev, nface)]
     alg = {k: sum(a[k] for a in ab) for k in ab[0]}  # bytes per step
-    default_plan = not (args.fused or args.occ or args.cmp_level or args.seg_level or args.seg_events)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": kernel_traffic(npts, dists, default_plan), "kernel": "k_level (one thread per merge)",
+                "traffic": kernel_traffic(npts, dists, default_plan and not tuned_knobs),
+                "kernel": "k_level (one thread per merge)",
                 "levels": [klev[0], klev[-1]] if klev else [], "launches_per_step": k_launches,
                 "alg_bytes_per_launch": k_bytes / max(k_launches, 1), "ms_per_launch": k_ms / max(k_launches, 1),
                 "peak_kind": peak_kind,
@@ -597,7 +779,24 @@ def main():
                 "phase_gbs": {k: alg[k] / (phase_ms[k] / steps / 1e3) / 1e9 for k in alg if phase_ms[k] > 0}}
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     sm_mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0
-    roofline["issue"] = kernel_issue(k_ms / max(k_launches, 1), sms, float(sm_mhz), npts, dists, default_plan)
+    roofline["issue"] = kernel_issue(k_ms / max(k_launches, 1), sms, float(sm_mhz), npts, dists,
+                                     default_plan and not tuned_knobs)
+    autotune_rec = {"knobs": tuned_knobs, "source": "autotuner cache" if tuned_knobs else "library defaults"}
+    if tuned_knobs:  # the same steps on a plan with the library defaults, for comparison
+        dplan = hull3d.Hull3D(npts)
+        for _ in range(2):
+            for x, f, nf, st in zip(dev_clouds, faces, nfs, sts):
+                dplan.compute_async(x, f, nf, st, stream)
+        torch.cuda.synchronize()
+        d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
+        for _ in range(args.steps):
+            for x, f, nf, st in zip(dev_clouds, faces, nfs, sts):
+                dplan.compute_async(x, f, nf, st, stream)
+        d1.record(stream)
+        torch.cuda.synchronize()
+        autotune_rec["default_value"] = len(clouds) * npts * args.steps / (d0.elapsed_time(d1) / 1e3) / 1e6
+        dplan.close()
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -605,7 +804,10 @@ def main():
             "config": {"workload": WORKLOAD, "n": npts, "clouds_per_step": len(clouds),
                        "faces": nface, "l2": "inputs larger than L2 (201 MB per cloud), no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline}
+            "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "autotune": autotune_rec}
+    if not args.no_extras and rank == 0:
+        line["adjacency"] = adjacency_leg(hull3d, torch, plan, faces, nfs, npts, stream)
+        line["delaunay"] = delaunay_leg(hull3d, torch, stream)
     if not args.no_batched:
         b = batched_leg(hull3d, torch, max(1, args.steps // 2),
                         cpu_baseline=rank == 0 and world == 1 and not args.no_cpu_baseline)
@@ -614,6 +816,8 @@ def main():
         line["batched"] = b
     if not args.no_serving and rank == 0:
         line["serving"] = serving_leg(hull3d, torch)
+    if not args.no_ablation and rank == 0:
+        line["float32_ablation"] = float32_ablation_leg(hull3d, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_leg()
     if rank == 0:

@@ -57,7 +57,8 @@ extern "C" {
 typedef struct hull3d_plan_s *hull3d_plan_t;
 
 /* Tuning knobs; zero fields mean "automatic" (hull3d_plan_opts reports the
- * resolved values).  None of them changes the result, only its speed. */
+ * resolved values).  None of them changes the result, only its speed, except
+ * float32_ablation, which exists to measure the paper's float arithmetic. */
 typedef struct {
     int32_t fused_levels;    /* bottom levels merged in one shared-memory kernel (1 = none, up to 10) */
     int32_t seg_level;       /* first level merged time-segment-parallel (> log2 n: never) */
@@ -76,7 +77,15 @@ typedef struct {
                                 or in x-order: -1 */
     int32_t seg_events_min;  /* shortest time window; a merge of E child events gets 2 sqrt(E) within
                                 [seg_events_min, seg_events] */
-    int32_t reserved[5];
+    int32_t batch_warp_nodes; /* batch kernel: levels of a cloud with fewer merges than this run one warp per
+                                 merge, the others one thread per merge (automatic: 64) */
+    int32_t multi_ranks;     /* batch calls: clouds above 4096 points are hulled together in groups whose
+                                aligned blocks fill at most this many ranks (automatic and at most: max_n) */
+    int32_t float32_ablation; /* 1: batch calls hull the clouds of at most 4096 points with the float32
+                                 arithmetic of the paper's GPU kernel (Sec. 3: cl_float coordinates) instead
+                                 of the exact predicates -- an ablation: the result need not be the hull,
+                                 and is the only knob here that can change it.  0: exact (default) */
+    int32_t reserved[2];
 } hull3d_opts;
 
 /* Creates a plan for hulls of up to max_n points (hull3d_compute*) and for
@@ -141,6 +150,25 @@ int hull3d_compute_host(hull3d_plan_t plan, const int32_t *h_xyz, int64_t n, int
 int hull3d_batch_async(hull3d_plan_t plan, const int32_t *d_xyz, const int64_t *h_offsets, int64_t B,
                        int32_t *d_faces, const int64_t *h_face_offsets, int64_t *d_nfaces, int32_t *d_status,
                        void *stream);
+
+/* 2D Delaunay triangulation through the lifting map: the points (x, y) are
+ * lifted to (x, y, x^2 + y^2), whose lower hull projects to the Delaunay
+ * triangulation, and the hull pipeline's lower pass (Sec. 2) computes it.
+ * This is an application of the paper's method, not a part of the paper.
+ *   d_xy      device, n x 2 int32, |x| and |y| < 2^15 (so x^2 + y^2 < 2^31)
+ *   d_tris    device, cap_tris x 3 int32 (cap_tris >= 2n - 4 for n >= 3):
+ *             triangles of input indices, counter-clockwise in the plane,
+ *             rotated min-first, sorted; the lower faces of zero area (points
+ *             on one edge of the convex hull) are not triangles and are left
+ *             out, so n points with h on the hull boundary give 2n - h - 2
+ *   d_ntris   device int64, the triangle count (may be NULL)
+ *   d_status  device int32, 0 or HULL3D_ERR_COORD_RANGE / _DUPLICATE /
+ *             _INTERNAL found on the device (may be NULL)
+ * Four or more cocircular points get one consistent triangulation (the
+ * perturbation of the hull decides).  Uses the plan's scratch; host-detected
+ * argument errors are returned before anything is enqueued. */
+int hull3d_delaunay_async(hull3d_plan_t plan, const int32_t *d_xy, int64_t n, int32_t *d_tris, int64_t cap_tris,
+                          int64_t *d_ntris, int32_t *d_status, void *stream);
 
 /* Adjacency of a hull: the arrangement structure (a doubly connected edge
  * list, in essence) that the paper names as the prerequisite for further

@@ -86,6 +86,7 @@ struct hull3d_plan_s {
     PassBufs pass[2]{};
     int32_t *status = nullptr;
     int64_t *nfaces = nullptr;
+    int64_t *items = nullptr;  // device count of a sort's items (Delaunay triangle keys)
     int32_t *stage_xyz = nullptr, *stage_faces = nullptr;
     // pinned host mirrors
     int64_t *h_nfaces = nullptr;
@@ -258,6 +259,7 @@ size_t layout(hull3d_plan_s *p, char *base)
     p->pass[1].lev_events = p->lev_stats + 64;
     p->status = b.take<int32_t>(1);
     p->nfaces = b.take<int64_t>(1);
+    p->items = b.take<int64_t>(1);
     p->stage_xyz = b.take<int32_t>(3 * N);
     p->stage_faces = b.take<int32_t>(3 * N2);
     return b.off;
@@ -341,6 +343,19 @@ const LevelOrder *level_order(const hull3d_plan_s *p, int level, const LevelOrde
     return (p->opts.merge_order >= 0 && level >= 3 && level <= 8) ? ord : nullptr;
 }
 int default_seg_events(const hull3d_plan_s *p) { return p->opts.seg_events > 0 ? p->opts.seg_events : 512; }
+// Longest time window of a level.  A window starts from both child hulls,
+// whose size grows as the square root of the merge's points, so the
+// start-hull entries of a level of merges of m points grow as m^1.5 while the
+// buffer for them is linear in n: above level 20 the windows double per level
+// (1024, 2048, then 4096 child events), which keeps the entries of merges of
+// up to 2^22 points on a paraboloid (2D Delaunay) inside the buffer; below it
+// 512 measured best (2^20 sphere).
+int seg_events_at(const hull3d_plan_s *p, int level)
+{
+    if (p->opts.seg_events > 0) return p->opts.seg_events;
+    if (level <= 20) return 512;
+    return level >= 23 ? 4096 : 512 << (level - 20);
+}
 int default_seg_events_min(const hull3d_plan_s *p)
 {
     const int K = default_seg_events(p);
@@ -348,6 +363,17 @@ int default_seg_events_min(const hull3d_plan_s *p)
     return k < K ? k : K;
 }
 int default_seg_slots(const hull3d_plan_s *p) { return p->opts.seg_slots > 0 ? p->opts.seg_slots : 1536; }
+// Batch kernel: one thread per merge while a level of a cloud has at least 64
+// merges, then one warp per merge (the tuner may pick another cut-over).
+int default_batch_warp_nodes(const hull3d_plan_s *p)
+{
+    return p->opts.batch_warp_nodes > 0 ? p->opts.batch_warp_nodes : 64;
+}
+// Rank space of one group of large clouds: the plan's max_n, or less.
+int64_t default_multi_ranks(const hull3d_plan_s *p)
+{
+    return (p->opts.multi_ranks > 0 && p->opts.multi_ranks < p->max_n) ? p->opts.multi_ranks : p->max_n;
+}
 
 // Records a phase-boundary event when profiling (one per boundary per call).
 int mark(hull3d_plan_s *p, cudaStream_t st, int *slot)
@@ -401,7 +427,7 @@ int enqueue_levels(hull3d_plan_s *p, const Points &pts, const Span &sp, int ncl,
                                           level_order(p, level, &ord), ab_level);
             }
             launch_seg_level(pts, sp, level, p->pass, p->seg, p->pk0, p->pv0, p->pk1, p->pv1, p->npairs, p->overflow,
-                             p->pair_cap, p->S_cap, p->M_cap, default_seg_events(p), default_seg_events_min(p),
+                             p->pair_cap, p->S_cap, p->M_cap, seg_events_at(p, level), default_seg_events_min(p),
                              default_seg_slots(p), min_ev, p->ss, status, st, launches);
         } else if (level >= default_cmp_level(p, LR)) {
             launch_level_cmp(pts, sp, level, p->pass, 2, status, st, default_cmp_slots(p));
@@ -431,14 +457,21 @@ int enqueue_hull(hull3d_plan_s *p, const int32_t *d_xyz, int64_t n, int32_t *d_f
     MARK(0);
     CK(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
     CK(cudaMemsetAsync(p->lev_stats, 0, 128 * sizeof(unsigned long long), st));
-    launch_keys(d_xyz, n, p->k0, p->v0, status, st);
-    launches++;
-    STEP("keys");
-    int which = radix_sort_pairs(p->k0, p->v0, p->k1, p->v1, n, nullptr, 63, p->ss, st, &launches);
-    STEP("point sort");
-    launch_decode(which ? p->k1 : p->k0, which ? p->v1 : p->v0, n, p->P4, status, st);
-    launches++;
-    STEP("decode");
+    int which = 0;
+    if (n <= SMALL_SORT_MAX) {  // one CTA: keys, sort, decode
+        launch_small_sort(d_xyz, n, p->P4, status, st);
+        launches++;
+        STEP("small sort");
+    } else {
+        launch_keys(d_xyz, n, p->k0, p->v0, status, st);
+        launches++;
+        STEP("keys");
+        which = radix_sort_pairs(p->k0, p->v0, p->k1, p->v1, n, nullptr, 63, p->ss, st, &launches);
+        STEP("point sort");
+        launch_decode(which ? p->k1 : p->k0, which ? p->v1 : p->v0, n, p->P4, status, st);
+        launches++;
+        STEP("decode");
+    }
     MARK(1);
     if (n < 3) {
         CK(cudaMemsetAsync(nf, 0, sizeof(int64_t), st));
@@ -471,11 +504,17 @@ int enqueue_hull(hull3d_plan_s *p, const int32_t *d_xyz, int64_t n, int32_t *d_f
     launch_face_keys(pts, n, L, p->pass, p->k0, p->v0, nf, status, st);
     launches++;
     STEP("face keys");
-    which = radix_sort_pairs(p->k0, p->v0, p->k1, p->v1, 2 * n, nf, 2 * fbits, p->ss, st, &launches);
-    STEP("face sort");
-    launch_face_out(which ? p->k1 : p->k0, which ? p->v1 : p->v0, 2 * n, fbits, nf, d_faces, st);
-    launches++;
-    STEP("face out");
+    if (n <= SMALL_SORT_MAX) {  // at most 2n - 4 faces: one CTA sorts them
+        launch_small_face_sort(p->k0, p->v0, fbits, nf, d_faces, st);
+        launches++;
+        STEP("small face sort");
+    } else {
+        which = radix_sort_pairs(p->k0, p->v0, p->k1, p->v1, 2 * n, nf, 2 * fbits, p->ss, st, &launches);
+        STEP("face sort");
+        launch_face_out(which ? p->k1 : p->k0, which ? p->v1 : p->v0, 2 * n, fbits, nf, d_faces, st);
+        launches++;
+        STEP("face out");
+    }
     MARK(5);
     if (p->profile) p->marks.insert(p->marks.end(), slots, slots + HULL3D_PHASES + 1);
     p->last_launches = launches;
@@ -560,6 +599,42 @@ int enqueue_multi(hull3d_plan_s *p, const int32_t *d_xyz, const int64_t *h_offse
     return e == cudaSuccess ? HULL3D_OK : cuda_fail(e);
 }
 
+// Enqueues the Delaunay triangulation of n 2D points through the lifting
+// map: lifted keys, the sort, every merge level (the lower pass gives the
+// triangles), the triangles' canonical sort.
+int enqueue_delaunay(hull3d_plan_s *p, const int32_t *d_xy, int64_t n, int32_t *d_tris, int64_t *nt, int32_t *status,
+                     cudaStream_t st)
+{
+    int64_t launches = 0;
+    CK(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
+    CK(cudaMemsetAsync(nt, 0, sizeof(int64_t), st));
+    CK(cudaMemsetAsync(p->lev_stats, 0, 128 * sizeof(unsigned long long), st));
+    launch_keys_lifted(d_xy, n, p->k0, p->v0, status, st);
+    int which = radix_sort_pairs(p->k0, p->v0, p->k1, p->v1, n, nullptr, 63, p->ss, st, &launches);
+    launch_decode_lifted(which ? p->k1 : p->k0, which ? p->v1 : p->v0, n, p->P4, status, st);
+    launches += 2;
+    if (n >= 3) {
+        const Points pts{ p->P4 };
+        const int L = ceil_log2(n);
+        const bool prof = p->profile;  // the per-call phase record belongs to hulls
+        p->profile = false;
+        int slots[HULL3D_PHASES + 1];
+        bool seg_marked = false;
+        int rc = enqueue_levels(p, pts, single_span(n), 1, L, 1, status, st, &launches, slots, &seg_marked);
+        p->profile = prof;
+        if (rc) return rc;
+        int fbits = ceil_log2(n);
+        if (fbits < 1) fbits = 1;
+        launch_tri_keys(pts, n, L, p->pass, p->k0, p->v0, p->items, nt, status, st);
+        which = radix_sort_pairs(p->k0, p->v0, p->k1, p->v1, 2 * n, p->items, 2 * fbits, p->ss, st, &launches);
+        launch_face_out(which ? p->k1 : p->k0, which ? p->v1 : p->v0, 2 * n, fbits, nt, d_tris, st);
+        launches += 2;
+    }
+    p->last_launches = launches;
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HULL3D_OK : cuda_fail(e);
+}
+
 bool use_graphs(const hull3d_plan_s *p) { return p->opts.use_graph >= 0 && !p->profile && !debug_sync(); }
 
 // Enqueues the pipeline as a replay of a cached CUDA graph (captured on the
@@ -621,7 +696,8 @@ int hull3d_plan(hull3d_plan_t *out, int64_t max_n, int64_t max_clouds, const hul
     p->max_n = max_n < 4 ? 4 : max_n;
     p->max_clouds = max_clouds;
     if (opts) p->opts = *opts;
-    if (p->opts.fused_levels < 0 || p->opts.fused_levels > 10 || p->opts.cmp_slots < 0 || p->opts.cmp_slots > 4096 ||
+    if (p->opts.float32_ablation < 0 || p->opts.float32_ablation > 1 || p->opts.fused_levels < 0 ||
+        p->opts.fused_levels > 10 || p->opts.cmp_slots < 0 || p->opts.cmp_slots > 4096 ||
         p->opts.seg_slots < 0 || p->opts.seg_slots > 6144 || p->opts.seg_events < 0 || p->opts.seg_events > 4096 ||
         p->opts.seg_events_min < 0) {
         delete p;
@@ -682,6 +758,8 @@ int hull3d_plan_opts(hull3d_plan_t p, hull3d_opts *out)
     out->seg_slots = default_seg_slots(p);
     out->seg_min_events = default_seg_min_events(p);
     out->merge_order = p->opts.merge_order < 0 ? -1 : 1;
+    out->batch_warp_nodes = default_batch_warp_nodes(p);
+    out->multi_ranks = (int32_t)std::min<int64_t>(default_multi_ranks(p), INT32_MAX);
     return HULL3D_OK;
 }
 
@@ -787,7 +865,7 @@ int hull3d_batch_async(hull3d_plan_t p, const int32_t *d_xyz, const int64_t *h_o
         const int count = (int)(end - begin);
         if (count <= 0) continue;
         launch_batch_class(c, d_xyz, p->b_off, p->b_foff, p->b_order + begin, count, p->b_counter + c, d_faces,
-                           d_nfaces, d_status, p->sms, st);
+                           d_nfaces, d_status, p->sms, default_batch_warp_nodes(p), p->opts.float32_ablation == 1, st);
         launches++;
     }
     // clouds above the largest class (ord holds them by decreasing size):
@@ -816,7 +894,7 @@ int hull3d_batch_async(hull3d_plan_t p, const int32_t *d_xyz, const int64_t *h_o
                 launches += p->last_launches;
                 continue;
             }
-            if (used + blk > p->max_n || (int64_t)group.size() + 1 > p->mt_cap) {
+            if (used + blk > default_multi_ranks(p) || (int64_t)group.size() + 1 > p->mt_cap) {
                 int rc = flush();
                 if (rc) return rc;
             }
@@ -830,6 +908,18 @@ int hull3d_batch_async(hull3d_plan_t p, const int32_t *d_xyz, const int64_t *h_o
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
     return HULL3D_OK;
+}
+
+int hull3d_delaunay_async(hull3d_plan_t p, const int32_t *d_xy, int64_t n, int32_t *d_tris, int64_t cap_tris,
+                          int64_t *d_ntris, int32_t *d_status, void *stream)
+{
+    if (!p || !d_xy || n < 1 || n > p->max_n) return HULL3D_ERR_INVALID_ARG;
+    if (n >= 3) {
+        if (!d_tris) return HULL3D_ERR_INVALID_ARG;
+        if (cap_tris < 2 * n - 4) return HULL3D_ERR_CAPACITY;
+    }
+    return enqueue_delaunay(p, d_xy, n, d_tris, d_ntris ? d_ntris : p->nfaces, d_status ? d_status : p->status,
+                            (cudaStream_t)stream);
 }
 
 int hull3d_adjacency_async(hull3d_plan_t p, const int32_t *d_faces, const int64_t *d_nfaces, int64_t cap_faces,

@@ -54,6 +54,19 @@ struct EqxTier<BPts> {
     static constexpr bool on = false;
 };
 
+// The same points under the float32 predicates of the paper's GPU kernel
+// (an ablation: how often float arithmetic gives a wrong hull).
+struct BPtsF : BPts {
+};
+template <>
+struct F32Pred<BPtsF> {
+    static constexpr bool on = true;
+};
+template <>
+struct EqxTier<BPtsF> {
+    static constexpr bool on = false;
+};
+
 struct BLinks {
     ushort2 *L;
     __device__ __forceinline__ static int un(unsigned short v) { return v == BNIL ? NIL : (int)v; }
@@ -159,12 +172,13 @@ constexpr int batch_ctas_per_sm()
     return (int)((233472 / (BatchSmem<NMAX>::bytes + 1024)) < 4 ? (233472 / (BatchSmem<NMAX>::bytes + 1024)) : 4);
 }
 
-template <int NMAX>
+template <int NMAX, class PTS>
 __global__ void __launch_bounds__(batch_threads<NMAX>(), batch_ctas_per_sm<NMAX>()) k_batch(const int32_t *__restrict__ xyz,
                                                          const int64_t *__restrict__ off,
                                                          const int64_t *__restrict__ foff,
                                                          const int32_t *__restrict__ order, int count, int *counter,
-                                                         int32_t *faces, int64_t *nfaces, int32_t *status)
+                                                         int32_t *faces, int64_t *nfaces, int32_t *status,
+                                                         int warp_nodes)
 {
     extern __shared__ __align__(16) unsigned char bsm[];
     __shared__ int s_cloud, s_err, s_kl;
@@ -215,7 +229,10 @@ __global__ void __launch_bounds__(batch_threads<NMAX>(), batch_ctas_per_sm<NMAX>
             unsigned short *C0 = W1 + 2 * NMAX, *C1 = C0 + NMAX;
             int L = 0;
             while ((1 << L) < n) L++;
-            const BPts sp{ K, ID };
+            PTS sp_;
+            sp_.K = K;
+            sp_.ID = ID;
+            const PTS &sp = sp_;
             BLinks lk{ LK };
             for (int pass = 0; pass < 2; pass++) {
                 const bool upper = pass != 0;
@@ -230,7 +247,7 @@ __global__ void __launch_bounds__(batch_threads<NMAX>(), batch_ctas_per_sm<NMAX>
                     const int half = 1 << (level - 1);
                     const int nodes = (n + 2 * half - 1) / (2 * half);
                     const bool root = level == L;
-                    if (nodes >= 64) {  // one thread per merge
+                    if (nodes >= warp_nodes) {  // one thread per merge
                         for (int t = tid; t < nodes; t += blockDim.x) {
                             const int llo = t * 2 * half, lmid = llo + half, lhi = min(llo + 2 * half, n);
                             if (lmid >= lhi) {
@@ -322,39 +339,58 @@ __global__ void __launch_bounds__(batch_threads<NMAX>(), batch_ctas_per_sm<NMAX>
     }
 }
 
-template <int NMAX>
+template <int NMAX, class PTS>
 static void launch_class(const int32_t *xyz, const int64_t *off, const int64_t *foff, const int32_t *order, int count,
-                         int *counter, int32_t *faces, int64_t *nfaces, int32_t *status, int sms, cudaStream_t st)
+                         int *counter, int32_t *faces, int64_t *nfaces, int32_t *status, int sms, int warp_nodes,
+                         cudaStream_t st)
 {
     if (count <= 0) return;
     const size_t smem = BatchSmem<NMAX>::bytes;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<NMAX>, batch_threads<NMAX>(), smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<NMAX, PTS>, batch_threads<NMAX>(), smem);
     if (per_sm < 1) per_sm = 1;
     int grid = sms * per_sm;
     if (grid > count) grid = count;
-    k_batch<NMAX><<<grid, batch_threads<NMAX>(), smem, st>>>(xyz, off, foff, order, count, counter, faces, nfaces,
-                                                             status);
+    k_batch<NMAX, PTS><<<grid, batch_threads<NMAX>(), smem, st>>>(xyz, off, foff, order, count, counter, faces,
+                                                                  nfaces, status, warp_nodes);
+}
+
+template <class PTS>
+static void batch_attributes()
+{
+    cudaFuncSetAttribute(k_batch<256, PTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BatchSmem<256>::bytes);
+    cudaFuncSetAttribute(k_batch<1024, PTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BatchSmem<1024>::bytes);
+    cudaFuncSetAttribute(k_batch<2048, PTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BatchSmem<2048>::bytes);
+    cudaFuncSetAttribute(k_batch<4096, PTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BatchSmem<4096>::bytes);
 }
 
 void batch_kernel_attributes()
 {
-    cudaFuncSetAttribute(k_batch<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BatchSmem<256>::bytes);
-    cudaFuncSetAttribute(k_batch<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BatchSmem<1024>::bytes);
-    cudaFuncSetAttribute(k_batch<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BatchSmem<2048>::bytes);
-    cudaFuncSetAttribute(k_batch<4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BatchSmem<4096>::bytes);
+    batch_attributes<BPts>();
+    batch_attributes<BPtsF>();
 }
 
 int batch_class_limit(int c) { return c == 0 ? 256 : c == 1 ? 1024 : c == 2 ? 2048 : 4096; }
 
+template <class PTS>
+static void launch_batch_pts(int c, const int32_t *xyz, const int64_t *off, const int64_t *foff, const int32_t *order,
+                             int count, int *counter, int32_t *faces, int64_t *nfaces, int32_t *status, int sms,
+                             int w, cudaStream_t st)
+{
+    if (c == 0) launch_class<256, PTS>(xyz, off, foff, order, count, counter, faces, nfaces, status, sms, w, st);
+    else if (c == 1) launch_class<1024, PTS>(xyz, off, foff, order, count, counter, faces, nfaces, status, sms, w, st);
+    else if (c == 2) launch_class<2048, PTS>(xyz, off, foff, order, count, counter, faces, nfaces, status, sms, w, st);
+    else launch_class<4096, PTS>(xyz, off, foff, order, count, counter, faces, nfaces, status, sms, w, st);
+}
+
 void launch_batch_class(int c, const int32_t *xyz, const int64_t *off, const int64_t *foff, const int32_t *order,
                         int count, int *counter, int32_t *faces, int64_t *nfaces, int32_t *status, int sms,
-                        cudaStream_t st)
+                        int warp_nodes, bool f32, cudaStream_t st)
 {
-    if (c == 0) launch_class<256>(xyz, off, foff, order, count, counter, faces, nfaces, status, sms, st);
-    else if (c == 1) launch_class<1024>(xyz, off, foff, order, count, counter, faces, nfaces, status, sms, st);
-    else if (c == 2) launch_class<2048>(xyz, off, foff, order, count, counter, faces, nfaces, status, sms, st);
-    else launch_class<4096>(xyz, off, foff, order, count, counter, faces, nfaces, status, sms, st);
+    if (f32)
+        launch_batch_pts<BPtsF>(c, xyz, off, foff, order, count, counter, faces, nfaces, status, sms, warp_nodes, st);
+    else
+        launch_batch_pts<BPts>(c, xyz, off, foff, order, count, counter, faces, nfaces, status, sms, warp_nodes, st);
 }
 
 }  // namespace hull3d

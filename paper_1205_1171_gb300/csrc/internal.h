@@ -23,12 +23,28 @@ constexpr int SORT_TILE = 4096;  // keys per CTA tile (256 threads x 16)
 int radix_sort_pairs(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int64_t n, const int64_t *d_n,
                      int bits, const SortScratch &s, cudaStream_t st, int64_t *launches);
 
+// A1 + A2 for n <= SMALL_SORT_MAX in one CTA (keys, bitonic sort in shared
+// memory, decode, duplicates), and the canonical sort of such a hull's faces
+// (keys and values as for launch_face_out; *d_nf <= 2 SMALL_SORT_MAX).
+constexpr int SMALL_SORT_MAX = 4096;
+constexpr int SMALL_SORT_THREADS = 1024;
+void launch_small_sort(const int32_t *xyz, int64_t n, int4 *P, int32_t *status, cudaStream_t st);
+void launch_small_face_sort(const uint64_t *keys, const uint32_t *vals, int fbits, const int64_t *d_nf,
+                            int32_t *faces, cudaStream_t st);
+
 // A1: range check and key build: key = (x + 2^20) << 42 | (z + 2^20) << 21 | (y + 2^20).
 void launch_keys(const int32_t *xyz, int64_t n, uint64_t *keys, uint32_t *vals, int32_t *status, cudaStream_t st);
 
 // After the sort: decode the sorted keys to rank-ordered points (x, y, z, input
 // index) and flag duplicates.
 void launch_decode(const uint64_t *keys, const uint32_t *vals, int64_t n, int4 *P, int32_t *status, cudaStream_t st);
+
+// The same for 2D points (n x 2 int32, |x|, |y| < 2^15) lifted to
+// (x, y, x^2 + y^2): key (x + 2^15) << 47 | z << 16 | (y + 2^15).
+void launch_keys_lifted(const int32_t *xy, int64_t n, uint64_t *keys, uint32_t *vals, int32_t *status,
+                        cudaStream_t st);
+void launch_decode_lifted(const uint64_t *keys, const uint32_t *vals, int64_t n, int4 *P, int32_t *status,
+                          cudaStream_t st);
 
 // Event-list storage of one pass: two ping-pong buffers (W with the insert flag, A, B) and counts by node lo.
 struct PassBufs {
@@ -97,6 +113,12 @@ void launch_seg_level(const Points &pts, const Span &sp, int level, PassBufs *pa
 void launch_face_keys(const Points &pts, int64_t n, int level, PassBufs *passes, uint64_t *keys, uint32_t *vals,
                       int64_t *d_nfaces, int32_t *status, cudaStream_t st);
 
+// Delaunay triangles of lifted points from the lower pass's root movie (see
+// k_tri_keys): keys as launch_face_keys, *d_items keys written (zero-area
+// ones with the largest key), *d_ntris the triangles (must start at 0).
+void launch_tri_keys(const Points &pts, int64_t n, int level, PassBufs *passes, uint64_t *keys, uint32_t *vals,
+                     int64_t *d_items, int64_t *d_ntris, int32_t *status, cudaStream_t st);
+
 // Sorted face keys -> int32 x 3 output rows (key = f0 << fbits | f1, fbits = ceil(log2 n)).
 void launch_face_out(const uint64_t *keys, const uint32_t *vals, int64_t cap, int fbits, const int64_t *d_nfaces,
                      int32_t *faces, cudaStream_t st);
@@ -160,8 +182,10 @@ int launch_multi_faces(const Points &pts, const MultiTables &t, int C, int fbits
 // listed in order[] (cloud indices into off/foff), pulling work from *counter.
 constexpr int BATCH_CLASSES = 4;
 int batch_class_limit(int c);
+// Levels of a cloud with fewer than warp_nodes merges run one warp per merge.
+// f32: the float32 predicate ablation instead of the exact predicates.
 void launch_batch_class(int c, const int32_t *xyz, const int64_t *off, const int64_t *foff, const int32_t *order,
                         int count, int *counter, int32_t *faces, int64_t *nfaces, int32_t *status, int sms,
-                        cudaStream_t st);
+                        int warp_nodes, bool f32, cudaStream_t st);
 
 }  // namespace hull3d

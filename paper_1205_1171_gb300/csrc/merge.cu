@@ -537,6 +537,53 @@ __global__ void k_face_keys(Points pts, int64_t n, int level, PassBufs p0, PassB
     }
 }
 
+// Delaunay triangles: the lower pass's root events (a, w, b) whose points are
+// not collinear in the plane, counter-clockwise in the plane, rotated
+// min-first; zero-area events (a sliver the perturbation makes of points on
+// one edge of the convex hull) get the largest key and are not counted.
+// *d_items = the lower event count (keys written), *d_ntris = the triangles.
+__global__ void k_tri_keys(Points pts, int64_t n, int level, PassBufs p0, int fbits, uint64_t *keys, uint32_t *vals,
+                           int64_t *d_items, int64_t *d_ntris, int32_t *status)
+{
+    const int buf = level & 1;
+    const int kl = p0.cnt[buf][0];
+    const bool bad = (int64_t)kl > 2 * n - 4;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (bad) set_status2(status, HULL3D_ERR_INTERNAL);
+        *d_items = (*status || bad) ? 0 : kl;
+    }
+    if (*status || bad) return;
+    GPts gp{ pts.P };
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < kl; e += (int64_t)gridDim.x * blockDim.x) {
+        const P3 A = gp.get(p0.A[buf][e]), W = gp.get((int)(p0.W[buf][e] & RANK_MASK)), B = gp.get(p0.B[buf][e]);
+        const long long area = (long long)(W.x - A.x) * (B.y - A.y) - (long long)(B.x - A.x) * (W.y - A.y);
+        if (area == 0) {
+            keys[e] = ~0ull;
+            vals[e] = 0;
+            continue;
+        }
+        int f0 = A.id, f1, f2;
+        if (area > 0) { f1 = W.id; f2 = B.id; } else { f1 = B.id; f2 = W.id; }
+        if (f1 < f0 && f1 < f2) { int t = f0; f0 = f1; f1 = f2; f2 = t; }
+        else if (f2 < f0 && f2 < f1) { int t = f2; f2 = f1; f1 = f0; f0 = t; }
+        keys[e] = ((uint64_t)f0 << fbits) | (uint64_t)f1;
+        vals[e] = (uint32_t)f2;
+        atomicAdd((unsigned long long *)d_ntris, 1ull);
+    }
+}
+
+static int face_grid();
+
+void launch_tri_keys(const Points &pts, int64_t n, int level, PassBufs *passes, uint64_t *keys, uint32_t *vals,
+                     int64_t *d_items, int64_t *d_ntris, int32_t *status, cudaStream_t st)
+{
+    int fbits = 1;
+    while ((1ll << fbits) < n) fbits++;
+    const int64_t need = (n + 255) / 256;
+    const unsigned gx = (unsigned)(need < face_grid() ? need : face_grid());
+    k_tri_keys<<<gx, 256, 0, st>>>(pts, n, level, passes[0], fbits, keys, vals, d_items, d_ntris, status);
+}
+
 static int face_grid()
 {
     static int g = 0;

@@ -37,12 +37,34 @@ struct Tri {
     long long Z, Y, Nx;
 };
 
+// Whether the predicates for points of type PT are the float32 arithmetic of
+// the paper's GPU kernel (cl_float coordinates, Sec. 3) instead of the exact
+// perturbed ones: an ablation only, whose results need not be a hull.  A
+// point type opts in by specialising this.
+template <class PT>
+struct F32Pred {
+    static constexpr bool on = false;
+};
+
+__device__ __forceinline__ int sgnf(float v) { return (v > 0.f) - (v < 0.f); }
+
 template <class PT>
 __device__ __forceinline__ void tri_make(const PT &pt, Tri &t, int p, int q, int r)
 {
     t.p = p; t.q = q; t.r = r;
     if ((p | q | r) < 0) { t.s = 0; return; }
     P3 P = pt.get(p), Q = pt.get(q), R = pt.get(r);
+    if constexpr (F32Pred<PT>::on) {
+        // the time of the triple as the float quotient Z / Y of float cross
+        // products; Y == 0 (collinear in the -infinity view) has no event
+        const float ax = (float)Q.x - (float)P.x, ay = (float)Q.y - (float)P.y, az = (float)Q.z - (float)P.z;
+        const float bx = (float)R.x - (float)P.x, by = (float)R.y - (float)P.y, bz = (float)R.z - (float)P.z;
+        const float Z = ax * bz - bx * az, Y = ax * by - bx * ay;
+        t.s = sgnf(Y);
+        t.Z = (long long)__float_as_uint(t.s ? Z / Y : 0.f);
+        t.Y = t.Nx = 0;
+        return;
+    }
     long long ax = Q.x - P.x, ay = Q.y - P.y, az = Q.z - P.z;
     long long bx = R.x - P.x, by = R.y - P.y, bz = R.z - P.z;
     t.Z = ax * bz - bx * az;
@@ -72,6 +94,11 @@ template <class PT>
 __device__ __forceinline__ int tri_cmp(const PT &pt, const Tri &a, const Tri &b, bool upper)
 {
     int s;
+    if constexpr (F32Pred<PT>::on) {  // float times, equal times compare equal
+        const float ta = __uint_as_float((unsigned)a.Z), tb = __uint_as_float((unsigned)b.Z);
+        s = (ta > tb) - (ta < tb);
+        return upper ? -s : s;
+    }
     const i128 D0 = (i128)a.Z * b.Y - (i128)b.Z * a.Y;
     if (D0 != 0) s = sgn128(D0) * a.s * b.s;
     else if (a.p == b.p && a.q == b.q && a.r == b.r) s = 0;
@@ -92,6 +119,12 @@ __device__ __forceinline__ int tri_cmp(const PT &pt, const Tri &a, const Tri &b,
 template <class PT>
 __device__ __forceinline__ int turn3(const PT &pt, int p, int q, int r)
 {
+    if constexpr (F32Pred<PT>::on) {  // float cross product of the (x, y) projection
+        const P3 P = pt.get(p), Q = pt.get(q), R = pt.get(r);
+        const float ax = (float)Q.x - (float)P.x, ay = (float)Q.y - (float)P.y;
+        const float bx = (float)R.x - (float)P.x, by = (float)R.y - (float)P.y;
+        return sgnf(ax * by - bx * ay);
+    }
     return turn_sign(pt.get(p), pt.get(q), pt.get(r));
 }
 

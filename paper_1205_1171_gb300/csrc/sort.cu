@@ -53,6 +53,145 @@ void launch_decode(const uint64_t *keys, const uint32_t *vals, int64_t n, int4 *
 }
 
 // ---------------------------------------------------------------------------
+// Small clouds (n <= SMALL_SORT_MAX): the key build, the sort, the decode and
+// the duplicate check in one CTA, the keys sorted by a bitonic network in
+// shared memory; and the canonical face sort of such a hull (at most
+// 2 SMALL_SORT_MAX - 4 faces) the same way.  Two launches instead of the
+// radix sort's three per pass.
+// ---------------------------------------------------------------------------
+template <class V>
+__device__ void bitonic_block(uint64_t *k, V *v, int m)
+{
+    for (int size = 2; size <= m; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < (m >> 1); t += blockDim.x) {
+                const int i = 2 * t - (t & (stride - 1)), j = i + stride;
+                if ((k[i] > k[j]) == ((i & size) == 0)) {
+                    const uint64_t tk = k[i]; k[i] = k[j]; k[j] = tk;
+                    const V tv = v[i]; v[i] = v[j]; v[j] = tv;
+                }
+            }
+            __syncthreads();
+        }
+}
+
+__global__ void __launch_bounds__(SMALL_SORT_THREADS) k_small_sort(const int32_t *__restrict__ xyz, int n,
+                                                                    int4 *__restrict__ P, int32_t *status)
+{
+    __shared__ uint64_t K[SMALL_SORT_MAX];
+    __shared__ unsigned short V[SMALL_SORT_MAX];
+    int m = 1;
+    while (m < n) m <<= 1;
+    const int lo = -(1 << 20), hi = (1 << 20) - 1;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        if (i < n) {
+            const int x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+            if (x < lo || x > hi || y < lo || y > hi || z < lo || z > hi) set_status(status, HULL3D_ERR_COORD_RANGE);
+            K[i] = ((uint64_t)((x - lo) & 0x1fffff) << 42) | ((uint64_t)((z - lo) & 0x1fffff) << 21) |
+                   (uint64_t)((y - lo) & 0x1fffff);
+        } else {
+            K[i] = ~0ull;
+        }
+        V[i] = (unsigned short)i;
+    }
+    __syncthreads();
+    bitonic_block(K, V, m);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint64_t k = K[i];
+        P[i] = make_int4((int)((k >> 42) & 0x1fffff) + lo, (int)(k & 0x1fffff) + lo, (int)((k >> 21) & 0x1fffff) + lo,
+                         (int)V[i]);
+        if (i > 0 && K[i - 1] == k) set_status(status, HULL3D_ERR_DUPLICATE);
+    }
+}
+
+void launch_small_sort(const int32_t *xyz, int64_t n, int4 *P, int32_t *status, cudaStream_t st)
+{
+    k_small_sort<<<1, SMALL_SORT_THREADS, 0, st>>>(xyz, (int)n, P, status);
+}
+
+constexpr int SMALL_FACES = 2 * SMALL_SORT_MAX;
+constexpr size_t SMALL_FACE_SMEM = (size_t)SMALL_FACES * (sizeof(uint64_t) + sizeof(uint32_t));
+
+// keys f0 << fbits | f1 and values f2 of *d_nf faces -> sorted int32 x 3 rows
+__global__ void __launch_bounds__(SMALL_SORT_THREADS) k_small_face_sort(const uint64_t *__restrict__ keys,
+                                                                         const uint32_t *__restrict__ vals, int fbits,
+                                                                         const int64_t *d_nf, int32_t *faces)
+{
+    extern __shared__ __align__(16) unsigned char fsm[];
+    uint64_t *K = (uint64_t *)fsm;
+    uint32_t *V = (uint32_t *)(K + SMALL_FACES);
+    const int nf = (int)min(*d_nf, (int64_t)SMALL_FACES);
+    int m = 1;
+    while (m < nf) m <<= 1;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        K[i] = i < nf ? keys[i] : ~0ull;
+        V[i] = i < nf ? vals[i] : 0u;
+    }
+    __syncthreads();
+    bitonic_block(K, V, m);
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+        const uint64_t k = K[i];
+        faces[3 * i] = (int32_t)(k >> fbits);
+        faces[3 * i + 1] = (int32_t)(k & ((1ull << fbits) - 1));
+        faces[3 * i + 2] = (int32_t)V[i];
+    }
+}
+
+void launch_small_face_sort(const uint64_t *keys, const uint32_t *vals, int fbits, const int64_t *d_nf,
+                            int32_t *faces, cudaStream_t st)
+{
+    k_small_face_sort<<<1, SMALL_SORT_THREADS, SMALL_FACE_SMEM, st>>>(keys, vals, fbits, d_nf, faces);
+}
+
+// ---------------------------------------------------------------------------
+// 2D points lifted to the paraboloid (x, y, x^2 + y^2) for the Delaunay
+// triangulation: |x|, |y| < 2^15, so z < 2^31 and the x-order key (x, z, y)
+// packs into 16 + 31 + 16 bits.
+// ---------------------------------------------------------------------------
+constexpr int LIFT_LIM = (1 << 15) - 1;
+
+__global__ void k_keys_lifted(const int32_t *__restrict__ xy, int64_t n, uint64_t *__restrict__ keys,
+                              uint32_t *__restrict__ vals, int32_t *status)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int x = xy[2 * i], y = xy[2 * i + 1];
+    if (x < -LIFT_LIM || x > LIFT_LIM || y < -LIFT_LIM || y > LIFT_LIM) {
+        set_status(status, HULL3D_ERR_COORD_RANGE);
+        keys[i] = 0;
+    } else {
+        const uint64_t z = (uint64_t)((int64_t)x * x + (int64_t)y * y);
+        keys[i] = ((uint64_t)(x + (1 << 15)) << 47) | (z << 16) | (uint64_t)(y + (1 << 15));
+    }
+    vals[i] = (uint32_t)i;
+}
+
+void launch_keys_lifted(const int32_t *xy, int64_t n, uint64_t *keys, uint32_t *vals, int32_t *status,
+                        cudaStream_t st)
+{
+    if (n <= 0) return;
+    k_keys_lifted<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(xy, n, keys, vals, status);
+}
+
+__global__ void k_decode_lifted(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t n,
+                                int4 *__restrict__ P, int32_t *status)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t k = keys[i];
+    P[i] = make_int4((int)(k >> 47) - (1 << 15), (int)(k & 0xffff) - (1 << 15), (int)((k >> 16) & 0x7fffffff),
+                     (int32_t)vals[i]);
+    if (i > 0 && keys[i - 1] == k) set_status(status, HULL3D_ERR_DUPLICATE);
+}
+
+void launch_decode_lifted(const uint64_t *keys, const uint32_t *vals, int64_t n, int4 *P, int32_t *status,
+                          cudaStream_t st)
+{
+    if (n <= 0) return;
+    k_decode_lifted<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(keys, vals, n, P, status);
+}
+
+// ---------------------------------------------------------------------------
 // LSD radix sort, 8-bit digits, 3 kernels per pass:
 //   hist    per-tile digit histogram -> hist[digit * T + tile]
 //   rowscan per-digit exclusive scan over tiles, row totals -> rowsum[digit]
@@ -255,6 +394,7 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_rs_scatter(const uint64_t *__
 void sort_kernel_attributes()
 {
     cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_STAGE_BYTES);
+    cudaFuncSetAttribute(k_small_face_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMALL_FACE_SMEM);
 }
 
 int radix_sort_pairs(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int64_t n, const int64_t *d_n,

@@ -36,7 +36,7 @@ EXPORTS = (
     "hull3d_plan", "hull3d_plan_opts", "hull3d_destroy", "hull3d_plan_bytes", "hull3d_compute_async", "hull3d_compute",
     "hull3d_compute_host", "hull3d_batch_async", "hull3d_strerror", "hull3d_last_cuda_error",
     "hull3d_last_launch_count", "hull3d_compute_static", "hull3d_profile", "hull3d_profile_read", "hull3d_profile_levels",
-    "hull3d_level_events", "hull3d_adjacency_async",
+    "hull3d_level_events", "hull3d_adjacency_async", "hull3d_delaunay_async",
 )
 PHASES = ("sort", "fused", "levels", "seg", "faces")
 
@@ -52,11 +52,12 @@ class Hull3DError(RuntimeError):
 
 
 OPT_NAMES = ("fused_levels", "seg_level", "seg_events", "use_graph", "level_occupancy", "cmp_level", "cmp_slots",
-             "seg_slots", "seg_min_events", "merge_order", "seg_events_min")
+             "seg_slots", "seg_min_events", "merge_order", "seg_events_min", "batch_warp_nodes", "multi_ranks",
+             "float32_ablation")
 
 
 class Opts(ctypes.Structure):
-    _fields_ = [(k, ctypes.c_int32) for k in OPT_NAMES] + [("reserved", ctypes.c_int32 * 5)]
+    _fields_ = [(k, ctypes.c_int32) for k in OPT_NAMES] + [("reserved", ctypes.c_int32 * 2)]
 
 
 def load():
@@ -84,6 +85,8 @@ def load():
             lib.hull3d_compute_host.restype = ctypes.c_int
             lib.hull3d_batch_async.argtypes = [P, P, P, i64, P, P, P, P, P]
             lib.hull3d_batch_async.restype = ctypes.c_int
+            lib.hull3d_delaunay_async.argtypes = [P, P, i64, P, i64, P, P, P]
+            lib.hull3d_delaunay_async.restype = ctypes.c_int
             lib.hull3d_adjacency_async.argtypes = [P, P, P, i64, i64, P, P, P, P, P]
             lib.hull3d_adjacency_async.restype = ctypes.c_int
             lib.hull3d_compute_static.argtypes = [P, i64, P, i64, P, P, P]
@@ -148,16 +151,22 @@ class Hull3D:
         self.max_n = int(max_n)
 
     @classmethod
-    def tuned(cls, max_n: int, max_clouds: int = 0, cache: str | None = None, **overrides):
-        """A plan with the knobs the autotuner stored for this GPU and size (the
-        library defaults when nothing was tuned); explicit overrides win."""
+    def tuned(cls, max_n: int, max_clouds: int = 0, cache: str | None = None, dist_class: str | None = None,
+              kind: str = "single", **overrides):
+        """A plan with the knobs the autotuner stored for this GPU, size,
+        distribution class ("volume" or "surface") and kind of work ("single"
+        hulls, "batch" of small clouds, "multi": groups of large clouds); the
+        library defaults where nothing was tuned.  Explicit overrides win."""
         import torch
 
         from paper_1205_1171_gb300 import autotune
 
-        knobs = autotune.lookup(torch.cuda.get_device_name(), max_n, cache or autotune.DEFAULT_CACHE) or {}
+        knobs = autotune.lookup(torch.cuda.get_device_name(), max_n, cache or autotune.DEFAULT_CACHE, dist_class,
+                                kind) or {}
         knobs.update(overrides)
-        return cls(max_n, max_clouds, **knobs)
+        plan = cls(max_n, max_clouds, **knobs)
+        plan.tuned_knobs = knobs
+        return plan
 
     def close(self):
         if getattr(self, "_plan", None):
@@ -272,6 +281,39 @@ class Hull3D:
                                           _stream_ptr(stream))
         if rc:
             raise Hull3DError(rc, "batch_async")
+
+    def delaunay_async(self, xy, tris, d_ntris=None, d_status=None, stream=None) -> None:
+        """Enqueues the Delaunay triangulation of the (n, 2) int32 device tensor
+        xy (|x|, |y| < 2^15) into tris, a (cap, 3) int32 device tensor."""
+        import torch
+
+        if not isinstance(xy, torch.Tensor) or xy.dtype != torch.int32 or xy.dim() != 2 or xy.shape[1] != 2:
+            raise ValueError("points must be an (n, 2) int32 tensor")
+        if not xy.is_cuda:
+            raise ValueError("points must be on a CUDA device")
+        xy = xy.contiguous()
+        rc = self._lib.hull3d_delaunay_async(
+            self._plan, xy.data_ptr(), xy.shape[0], tris.data_ptr(), tris.shape[0],
+            None if d_ntris is None else d_ntris.data_ptr(), None if d_status is None else d_status.data_ptr(),
+            _stream_ptr(stream))
+        if rc:
+            raise Hull3DError(rc, "delaunay_async")
+
+    def delaunay(self, xy, stream=None):
+        """Delaunay triangles (T, 3) int32 on the device of xy (synchronous)."""
+        import torch
+
+        n = int(xy.shape[0])
+        dev = xy.device
+        tris = torch.empty((max(2 * n - 4, 1), 3), dtype=torch.int32, device=dev)
+        nt = torch.zeros(1, dtype=torch.int64, device=dev)
+        st = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.delaunay_async(xy, tris, nt, st, stream)
+        (stream or torch.cuda.current_stream(dev)).synchronize()
+        code = int(st.item())
+        if code:
+            raise Hull3DError(code, "delaunay")
+        return tris[: int(nt.item())]
 
     def adjacency_async(self, faces, d_nfaces, n: int, nb, star_off, star, d_status, stream=None) -> None:
         """Enqueues the face neighbours and vertex stars of the canonical face

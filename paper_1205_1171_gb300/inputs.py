@@ -14,6 +14,16 @@ points (duplicates are redrawn).  Distributions:
   rounded (almost every point on the hull);
 * ``gauss``  rint(N(0, (2^18)^2)) per coordinate, clipped to the cube (a few
   hundred points land on each clipping plane: coplanar hull facets).
+
+Planar point sets for the Delaunay triangulation (``planar_seeded``), int32
+(x, y) with |x|, |y| < 2^15, no duplicates:
+
+* ``square`` uniform integers in [-2^15 + 1, 2^15 - 1]^2;
+* ``disk``   square samples kept inside the radius 2^15 - 1;
+* ``gauss``  rint(N(0, (2^13)^2)) per coordinate, clipped to the square (points
+  on the clipping edges: collinear boundary runs);
+* ``grid``   distinct points of a jittered-free integer lattice with a random
+  origin and spacing (every four neighbours cocircular).
 """
 from __future__ import annotations
 
@@ -95,3 +105,45 @@ def batch(count: int, seed: int, lo_exp: float = 4.0, hi_exp: float = 12.0):
     offsets[1:] = np.cumsum(sizes)
     xyz = np.concatenate(parts) if parts else np.zeros((0, 3), np.int32)
     return np.ascontiguousarray(xyz, dtype=np.int32), offsets, [DISTS[k] for k in kinds]
+
+
+PLANAR = ("square", "disk", "gauss", "grid")
+PLIM = (1 << 15) - 1
+
+
+def _draw2(kind: str, m: int, rng: np.random.Generator) -> np.ndarray:
+    if kind == "square":
+        return rng.integers(-PLIM, PLIM + 1, size=(m, 2), dtype=np.int64)
+    if kind == "disk":
+        out = np.empty((0, 2), np.int64)
+        while out.shape[0] < m:
+            c = rng.integers(-PLIM, PLIM + 1, size=(max(2 * (m - out.shape[0]), 64), 2), dtype=np.int64)
+            out = np.concatenate([out, c[(c * c).sum(axis=1) < PLIM * PLIM]])
+        return out[:m]
+    if kind == "gauss":
+        return np.clip(np.rint(rng.standard_normal((m, 2)) * float(1 << 13)), -PLIM, PLIM).astype(np.int64)
+    raise ValueError(f"unknown planar distribution {kind!r}")
+
+
+def planar(kind: str, n: int, rng: np.random.Generator) -> np.ndarray:
+    """n distinct planar points of one kind, as an (n, 2) int32 array."""
+    if kind == "grid":
+        side = int(np.ceil(np.sqrt(n)))
+        step = max(1, min(int(rng.integers(1, 64)), (2 * PLIM) // max(side, 1)))
+        org = rng.integers(-PLIM, PLIM - step * side + 1, size=2)
+        g = np.stack(np.meshgrid(np.arange(side), np.arange(side), indexing="ij"), -1).reshape(-1, 2)[:n]
+        pts = org + step * g
+        return np.ascontiguousarray(pts[rng.permutation(n)], dtype=np.int32)
+    pts = _draw2(kind, n, rng)
+    for _ in range(1000):
+        _, first = np.unique(pts[:, 0] * (1 << 17) + pts[:, 1], return_index=True)
+        if first.size == n:
+            break
+        pts = np.concatenate([pts[np.sort(first)], _draw2(kind, n - first.size, rng)])
+    else:  # pragma: no cover
+        raise RuntimeError("could not draw distinct points")
+    return np.ascontiguousarray(pts, dtype=np.int32)
+
+
+def planar_seeded(kind: str, n: int, seed: int) -> np.ndarray:
+    return planar(kind, n, np.random.Generator(np.random.PCG64(seed)))

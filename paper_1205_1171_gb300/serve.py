@@ -92,7 +92,7 @@ class CudaBackend:
 
     def __init__(self, small_max: int = 4096, batch_points: int = 1 << 21, batch_clouds: int = 8192,
                  large_slots: int = 2, large_max: int = 1 << 18, large_rank_space: int = 1 << 21,
-                 large_clouds: int = 1024, device: str = "cuda"):
+                 large_clouds: int = 1024, device: str = "cuda", tuned: bool = True):
         import torch
 
         from paper_1205_1171_gb300 import hull3d
@@ -104,8 +104,13 @@ class CudaBackend:
             raise ValueError("the largest request must fit a large slot's rank space")
         dev = torch.device(device)
 
-        def slot(max_n, points, clouds):
-            return {"plan": hull3d.Hull3D(max_n, max_clouds=clouds),
+        def plan(max_n, clouds, kind):  # the autotuner's knobs for this kind of work, if any
+            if tuned:
+                return hull3d.Hull3D.tuned(max_n, max_clouds=clouds, kind=kind)
+            return hull3d.Hull3D(max_n, max_clouds=clouds)
+
+        def slot(max_n, points, clouds, kind):
+            return {"plan": plan(max_n, clouds, kind),
                     "stream": torch.cuda.Stream(dev),
                     "xyz": torch.empty((points, 3), dtype=torch.int32, device=dev),
                     "faces": torch.empty((2 * points, 3), dtype=torch.int32, device=dev),
@@ -117,9 +122,11 @@ class CudaBackend:
                     "h_st": torch.zeros(clouds, dtype=torch.int32).pin_memory(),
                     "busy": None}
 
-        self.batch_slots = [slot(small_max, batch_points, batch_clouds) for _ in range(2)]
+        self.batch_slots = [slot(small_max, batch_points, batch_clouds, "batch") for _ in range(2)]
         # a large batch holds at most large_rank_space points (their blocks fill that many ranks)
-        self.large_slots = [slot(large_rank_space, large_rank_space, large_clouds) for _ in range(large_slots)]
+        self.large_slots = [slot(large_rank_space, large_rank_space, large_clouds, "multi") for _ in range(large_slots)]
+        self.knobs = {"batch": getattr(self.batch_slots[0]["plan"], "tuned_knobs", {}),
+                      "multi": getattr(self.large_slots[0]["plan"], "tuned_knobs", {}) if self.large_slots else {}}
 
     def resident_bytes(self) -> int:
         b = 0

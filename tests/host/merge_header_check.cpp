@@ -32,6 +32,18 @@ struct int2 {
 };
 static inline int2 make_int2(int a, int b) { return int2{ a, b }; }
 static inline int __ffs(unsigned v) { return __builtin_ffs((int)v); }
+static inline unsigned __float_as_uint(float f)
+{
+    unsigned u;
+    std::memcpy(&u, &f, sizeof u);
+    return u;
+}
+static inline float __uint_as_float(unsigned u)
+{
+    float f;
+    std::memcpy(&f, &u, sizeof f);
+    return f;
+}
 
 #include "../../paper_1205_1171_gb300/csrc/merge.cuh"
 

@@ -32,3 +32,17 @@ def test_batch_shapes():
     sizes = np.diff(off)
     assert sizes.min() >= 16 and sizes.max() <= 4096
     assert set(kinds) <= set(inputs.DISTS)
+
+
+def test_planar_sets_are_distinct_in_range_and_seeded():
+    import numpy as np
+
+    from paper_1205_1171_gb300 import inputs
+
+    for kind in inputs.PLANAR:
+        for n in (1, 3, 257, 4000):
+            a = inputs.planar_seeded(kind, n, 17)
+            assert a.shape == (n, 2) and a.dtype == np.int32
+            assert np.abs(a).max() <= (1 << 15) - 1
+            assert len(np.unique(a, axis=0)) == n
+            assert np.array_equal(a, inputs.planar_seeded(kind, n, 17))
