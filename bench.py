@@ -45,19 +45,20 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# DRAM bytes (read + write) per launch of the thread-per-merge level kernel,
-# from one ncu capture of the n = 2^24 cube + Gaussian step (the command and
-# the per-level figures are in profiles/), valid for the merge sources whose
-# SHA-256 is recorded with it.
-KERNEL_TRAFFIC = {"bytes_per_launch": 3308055331, "sources_sha256": "d1db39329cecbb9da57792613d72f6e9714fc1588756eb2a5f24fb3869a1ade2"}
+# DRAM bytes (read + write) and instructions per launch of the thread-per-merge
+# level kernel (levels 3-12 of the two n = 2^24 clouds, 20 launches, averaged),
+# from one-pass ncu captures of `bench.py --profile-once` (the command and the
+# per-level figures are in profiles/), valid for the merge sources whose SHA-256
+# and the plan knobs that are recorded with them.  The instruction counts give
+# the second roofline: instruction issue, against 4 warp instructions per SM
+# per cycle (one per SM sub-partition).
+KERNEL_SOURCES_SHA = "bcf53818d5f4afdb746838f0454fc5377cdfc83e14b577167c137e10448a94ce"
+KERNEL_KNOBS = {"cmp_level": 13, "level_occupancy": 0, "seg_events": 256, "seg_level": 12, "seg_min_events": 0}
+KERNEL_TRAFFIC = {"bytes_per_launch": 2321678208, "sources_sha256": KERNEL_SOURCES_SHA, "knobs": KERNEL_KNOBS}
 TRAFFIC_SOURCES = ("paper_1205_1171_gb300/csrc/merge.cu", "paper_1205_1171_gb300/csrc/merge.cuh",
                    "paper_1205_1171_gb300/csrc/predicates.cuh")
-# Warp and thread instructions per launch of the same kernel on the same step,
-# from one ncu capture (smsp__inst_executed.sum, smsp__thread_inst_executed.sum),
-# valid for the same sources.  They give the second roofline: instruction issue,
-# against 4 warp instructions per SM per cycle (one per SM sub-partition).
-KERNEL_ISSUE = {"warp_inst_per_launch": 1577019952, "thread_inst_per_launch": 19200567168,
-                "sources_sha256": "d1db39329cecbb9da57792613d72f6e9714fc1588756eb2a5f24fb3869a1ade2"}
+KERNEL_ISSUE = {"warp_inst_per_launch": 1491222985, "thread_inst_per_launch": 16627608858,
+                "sources_sha256": KERNEL_SOURCES_SHA, "knobs": KERNEL_KNOBS}
 ISSUE_PER_SM_PER_CYCLE = 4
 
 
@@ -71,24 +72,24 @@ def sources_sha256() -> str:
     return h.hexdigest()
 
 
-def kernel_traffic(npts: int = 1 << 24, dists=DISTS, default_plan: bool = True):
+def _recorded_applies(rec, npts, dists, knobs) -> bool:
+    return (bool(rec) and npts == 1 << 24 and tuple(dists) == tuple(DISTS) and knobs == rec["knobs"]
+            and rec["sources_sha256"] == sources_sha256())
+
+
+def kernel_traffic(npts: int = 1 << 24, dists=DISTS, knobs=None):
     """The recorded DRAM traffic per launch: None once the kernel changed, and
-    None for any other workload or plan than the one it was captured on."""
-    if not default_plan or npts != 1 << 24 or tuple(dists) != tuple(DISTS):
-        return None
-    if not KERNEL_TRAFFIC or KERNEL_TRAFFIC["sources_sha256"] != sources_sha256():
-        return None
-    return KERNEL_TRAFFIC["bytes_per_launch"]
+    None for any other workload or plan knobs than the ones it was captured on."""
+    knobs = KERNEL_KNOBS if knobs is None else knobs
+    return KERNEL_TRAFFIC["bytes_per_launch"] if _recorded_applies(KERNEL_TRAFFIC, npts, dists, knobs) else None
 
 
-def kernel_issue(ms_per_launch: float, sms: int, sm_mhz: float, npts: int = 1 << 24, dists=DISTS,
-                 default_plan: bool = True):
+def kernel_issue(ms_per_launch: float, sms: int, sm_mhz: float, npts: int = 1 << 24, dists=DISTS, knobs=None):
     """The instruction-issue roofline of the thread-per-merge kernel from the
     recorded instruction counts and the live launch time, or None where the
-    counts do not apply (other workload, plan or sources)."""
-    if not default_plan or npts != 1 << 24 or tuple(dists) != tuple(DISTS):
-        return None
-    if not KERNEL_ISSUE or KERNEL_ISSUE["sources_sha256"] != sources_sha256() or ms_per_launch <= 0:
+    counts do not apply (other workload, plan knobs or sources)."""
+    knobs = KERNEL_KNOBS if knobs is None else knobs
+    if not _recorded_applies(KERNEL_ISSUE, npts, dists, knobs) or ms_per_launch <= 0:
         return None
     w = KERNEL_ISSUE["warp_inst_per_launch"]
     achieved = w / (ms_per_launch / 1e3) / 1e9
@@ -336,7 +337,7 @@ def batched_leg(hull3d, torch, steps: int, cpu_baseline: bool = False, clouds: i
         sizes = np.diff(off[: clouds + 1])
         foff = np.zeros(clouds + 1, np.int64)
         foff[1:] = np.cumsum(np.where(sizes >= 3, 2 * sizes - 4, 0))
-        plan = hull3d.Hull3D(4096, max_clouds=clouds)
+        plan = hull3d.Hull3D.tuned(4096, max_clouds=clouds, kind="batch")  # as the batched leg
         faces = torch.empty((int(foff[-1]), 3), dtype=torch.int32, device="cuda")
         nf = torch.zeros(clouds, dtype=torch.int64, device="cuda")
         st = torch.zeros(clouds, dtype=torch.int32, device="cuda")
@@ -661,6 +662,7 @@ def main():
     # GPU, size and distribution class; the library defaults where none)
     plan = hull3d.Hull3D.tuned(npts, dist_class="volume") if default_plan else hull3d.Hull3D(npts, **cli_knobs)
     tuned_knobs = getattr(plan, "tuned_knobs", {}) if default_plan else {}
+    plan_knobs = dict(tuned_knobs) if default_plan else {k: v for k, v in cli_knobs.items() if v}
     cap = 2 * npts - 4
     faces = [torch.empty((cap, 3), dtype=torch.int32, device="cuda") for _ in clouds]
     nfs = [torch.zeros(1, dtype=torch.int64, device="cuda") for _ in clouds]
@@ -765,7 +767,7 @@ def main():
     ab = [alg_bytes(npts, ev, plan.fused_levels_used, nf, o["seg_level"]) for ev, nf in zip(level_ev, nface)]
     alg = {k: sum(a[k] for a in ab) for k in ab[0]}  # bytes per step
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": kernel_traffic(npts, dists, default_plan and not tuned_knobs),
+                "traffic": kernel_traffic(npts, dists, plan_knobs),
                 "kernel": "k_level (one thread per merge)",
                 "levels": [klev[0], klev[-1]] if klev else [], "launches_per_step": k_launches,
                 "alg_bytes_per_launch": k_bytes / max(k_launches, 1), "ms_per_launch": k_ms / max(k_launches, 1),
@@ -779,8 +781,7 @@ def main():
                 "phase_gbs": {k: alg[k] / (phase_ms[k] / steps / 1e3) / 1e9 for k in alg if phase_ms[k] > 0}}
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     sm_mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0
-    roofline["issue"] = kernel_issue(k_ms / max(k_launches, 1), sms, float(sm_mhz), npts, dists,
-                                     default_plan and not tuned_knobs)
+    roofline["issue"] = kernel_issue(k_ms / max(k_launches, 1), sms, float(sm_mhz), npts, dists, plan_knobs)
     autotune_rec = {"knobs": tuned_knobs, "source": "autotuner cache" if tuned_knobs else "library defaults"}
     if tuned_knobs:  # the same steps on a plan with the library defaults, for comparison
         dplan = hull3d.Hull3D(npts)

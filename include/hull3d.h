@@ -85,7 +85,9 @@ typedef struct {
                                  arithmetic of the paper's GPU kernel (Sec. 3: cl_float coordinates) instead
                                  of the exact predicates -- an ablation: the result need not be the hull,
                                  and is the only knob here that can change it.  0: exact (default) */
-    int32_t reserved[2];
+    int32_t seg_slots_big;   /* shared-memory table size of the second round of time windows (<= 6144, automatic:
+                                6144); windows too large for it get slot tables in global memory */
+    int32_t reserved[1];
 } hull3d_opts;
 
 /* Creates a plan for hulls of up to max_n points (hull3d_compute*) and for

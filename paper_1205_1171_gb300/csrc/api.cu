@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <climits>
 #include <mutex>
 #include <new>
@@ -100,6 +101,7 @@ struct hull3d_plan_s {
     unsigned long long *npairs = nullptr;
     int *overflow = nullptr;
     int64_t pair_cap = 0, S_cap = 0, M_cap = 0;
+    SegTables gtab{};  // global-memory slot tables of the time windows too large for shared memory
     // phase profiling
     bool profile = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -219,6 +221,7 @@ size_t layout(hull3d_plan_s *p, char *base)
             if (s == 0) {
                 sb.wlist = b.take<unsigned>(2 * p->S_cap);
                 sb.flist = b.take<unsigned>(2 * p->S_cap);
+                sb.glist = b.take<unsigned>(2 * p->S_cap);
                 sb.mlist = b.take<unsigned>(2 * p->M_cap);
             }
         }
@@ -228,7 +231,14 @@ size_t layout(hull3d_plan_s *p, char *base)
             p->pv0 = b.take<uint32_t>(p->pair_cap);
             p->pv1 = b.take<uint32_t>(p->pair_cap);
             p->npairs = b.take<unsigned long long>(1);
-            p->overflow = b.take<int>(4);  // pair overflow, merges in windows, windows, windows to retry
+            // pair overflow, merges in windows, windows, windows to retry, windows for the global tables
+            p->overflow = b.take<int>(5);
+            // one global-memory slot table per SM for windows whose start hulls exceed the largest shared-memory
+            // table (hull-heavy clouds of 2^22 points and more): 32768 slots, windows of up to 4096 child events
+            p->gtab.cap = N >= (1 << 20) ? 32768 : 8192;
+            p->gtab.ctas = p->sms > 0 ? p->sms : 132;
+            p->gtab.stride = ((int64_t)seg_smem_bytes(p->gtab.cap, 4096) + 255) & ~(int64_t)255;
+            p->gtab.base = b.take<char>(p->gtab.stride * p->gtab.ctas);
             // the pair sort needs histogram space for pair_cap items
             int64_t tiles = (p->pair_cap + SORT_TILE - 1) / SORT_TILE;
             if (tiles > p->ss.max_tiles) {
@@ -346,15 +356,19 @@ int default_seg_events(const hull3d_plan_s *p) { return p->opts.seg_events > 0 ?
 // Longest time window of a level.  A window starts from both child hulls,
 // whose size grows as the square root of the merge's points, so the
 // start-hull entries of a level of merges of m points grow as m^1.5 while the
-// buffer for them is linear in n: above level 20 the windows double per level
-// (1024, 2048, then 4096 child events), which keeps the entries of merges of
-// up to 2^22 points on a paraboloid (2D Delaunay) inside the buffer; below it
-// 512 measured best (2^20 sphere).
-int seg_events_at(const hull3d_plan_s *p, int level)
+// buffer for them is linear in n: from a size on the windows double per level
+// (1024, 2048, then 4096 child events).  Points lifted to a paraboloid (2D
+// Delaunay) all lie on the lower hull and need that from level 21 (a 2^22-point
+// triangulation overflows the buffer with 512 and falls back to the serial
+// merge: 18.7 s instead of 0.48 s); the hull of points on a sphere, the worst
+// 3D case of the workloads, fits with 512 through level 22 (2^22 sphere: 376 ms
+// with 512, 422 ms with the longer windows) and needs it from level 23.
+int seg_events_at(const hull3d_plan_s *p, int level, bool lifted)
 {
     if (p->opts.seg_events > 0) return p->opts.seg_events;
-    if (level <= 20) return 512;
-    return level >= 23 ? 4096 : 512 << (level - 20);
+    const int from = lifted ? 21 : 23;
+    if (level < from) return 512;
+    return level >= from + 2 ? 4096 : 1024 << (level - from);
 }
 int default_seg_events_min(const hull3d_plan_s *p)
 {
@@ -363,6 +377,27 @@ int default_seg_events_min(const hull3d_plan_s *p)
     return k < K ? k : K;
 }
 int default_seg_slots(const hull3d_plan_s *p) { return p->opts.seg_slots > 0 ? p->opts.seg_slots : 1536; }
+int seg_events_at(const hull3d_plan_s *p, int level, bool lifted);
+// The first-round slot table of a level's time windows: its start hulls (two
+// child hulls, at most ~1.45 sqrt(m) points each on the workloads, m = 2^(level-1)
+// child points: points on a paraboloid; ~1.1 sqrt(m) on a sphere) plus the
+// points a window inserts (at most its length, 2 sqrt(E) for E <= 2^(level+1)
+// child events, within the level's limits).  4 sqrt(2^level) + that length
+// leaves about twice the room the hulls need; a window that does not fit goes
+// to the retry rounds.  Smaller tables put more windows on an SM (the register
+// limit allows 9 one-warp CTAs): 288 slots at level 10 instead of 1536.
+int seg_slots_at(const hull3d_plan_s *p, int level, bool lifted)
+{
+    const int d = default_seg_slots(p);
+    if (p->opts.seg_slots > 0) return d;
+    const int K = seg_events_at(p, level, lifted);
+    const int Kmin = p->opts.seg_events_min > 0 ? std::min(p->opts.seg_events_min, K) : std::min(128, K);
+    const double e = 2.0 * std::sqrt((double)(1ll << (level + 1)));
+    const int kl = (int)std::min<double>(K, std::max<double>(Kmin, e));
+    const int need = ((int)(4.0 * std::sqrt((double)(1ll << level))) + kl + 8 + 31) / 32 * 32;
+    return need < d ? need : d;
+}
+int default_seg_slots_big(const hull3d_plan_s *p) { return p->opts.seg_slots_big > 0 ? p->opts.seg_slots_big : 6144; }
 // Batch kernel: one thread per merge while a level of a cloud has at least 64
 // merges, then one warp per merge (the tuner may pick another cut-over).
 int default_batch_warp_nodes(const hull3d_plan_s *p)
@@ -399,7 +434,7 @@ int mark(hull3d_plan_s *p, cudaStream_t st, int *slot)
 // ncl clouds in aligned blocks): one launch sequence per level for every
 // node of every cloud at that level, with no host synchronisation.
 int enqueue_levels(hull3d_plan_s *p, const Points &pts, const Span &sp, int ncl, int L, int l1, int32_t *status,
-                   cudaStream_t st, int64_t *launches, int *slots, bool *seg_marked)
+                   cudaStream_t st, int64_t *launches, int *slots, bool *seg_marked, bool lifted = false)
 {
     const int64_t R = sp.n;  // the rank space: thresholds follow the merges a level holds
     const LevelOrder ord{ p->k0, p->k1, p->v0, p->v1, p->ss };
@@ -427,8 +462,9 @@ int enqueue_levels(hull3d_plan_s *p, const Points &pts, const Span &sp, int ncl,
                                           level_order(p, level, &ord), ab_level);
             }
             launch_seg_level(pts, sp, level, p->pass, p->seg, p->pk0, p->pv0, p->pk1, p->pv1, p->npairs, p->overflow,
-                             p->pair_cap, p->S_cap, p->M_cap, seg_events_at(p, level), default_seg_events_min(p),
-                             default_seg_slots(p), min_ev, p->ss, status, st, launches);
+                             p->pair_cap, p->S_cap, p->M_cap, seg_events_at(p, level, lifted), default_seg_events_min(p),
+                             seg_slots_at(p, level, lifted), default_seg_slots_big(p), min_ev, p->ss, p->gtab, status,
+                             st, launches);
         } else if (level >= default_cmp_level(p, LR)) {
             launch_level_cmp(pts, sp, level, p->pass, 2, status, st, default_cmp_slots(p));
             *launches += 1;
@@ -620,7 +656,7 @@ int enqueue_delaunay(hull3d_plan_s *p, const int32_t *d_xy, int64_t n, int32_t *
         p->profile = false;
         int slots[HULL3D_PHASES + 1];
         bool seg_marked = false;
-        int rc = enqueue_levels(p, pts, single_span(n), 1, L, 1, status, st, &launches, slots, &seg_marked);
+        int rc = enqueue_levels(p, pts, single_span(n), 1, L, 1, status, st, &launches, slots, &seg_marked, true);
         p->profile = prof;
         if (rc) return rc;
         int fbits = ceil_log2(n);
@@ -697,7 +733,8 @@ int hull3d_plan(hull3d_plan_t *out, int64_t max_n, int64_t max_clouds, const hul
     p->max_clouds = max_clouds;
     if (opts) p->opts = *opts;
     if (p->opts.float32_ablation < 0 || p->opts.float32_ablation > 1 || p->opts.fused_levels < 0 ||
-        p->opts.fused_levels > 10 || p->opts.cmp_slots < 0 || p->opts.cmp_slots > 4096 ||
+        p->opts.fused_levels > 10 || p->opts.cmp_slots < 0 || p->opts.cmp_slots > 4096 || p->opts.seg_slots_big < 0 ||
+        p->opts.seg_slots_big > 6144 ||
         p->opts.seg_slots < 0 || p->opts.seg_slots > 6144 || p->opts.seg_events < 0 || p->opts.seg_events > 4096 ||
         p->opts.seg_events_min < 0) {
         delete p;
@@ -756,6 +793,7 @@ int hull3d_plan_opts(hull3d_plan_t p, hull3d_opts *out)
     out->seg_events = default_seg_events(p);
     out->seg_events_min = default_seg_events_min(p);
     out->seg_slots = default_seg_slots(p);
+    out->seg_slots_big = default_seg_slots_big(p);
     out->seg_min_events = default_seg_min_events(p);
     out->merge_order = p->opts.merge_order < 0 ? -1 : 1;
     out->batch_warp_nodes = default_batch_warp_nodes(p);

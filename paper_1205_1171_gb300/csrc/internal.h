@@ -100,13 +100,25 @@ void launch_level_cmp(const Points &pts, const Span &sp, int level, PassBufs *pa
 int launch_passthrough(const Span &sp, int ncl, int level, PassBufs *passes, int32_t *status, cudaStream_t st);
 
 struct SegBufs;
+// Slot tables in global memory for time windows too large for shared memory:
+// ctas regions of stride bytes, each holding cap slots (base null: none).
+struct SegTables {
+    char *base;
+    int64_t stride;
+    int cap, ctas;
+};
+// Bytes of a window's slot table of scap slots for windows of up to K child events.
+size_t seg_smem_bytes(int scap, int K);
+
 // One level merged time-segment-parallel (windows of Kmin .. K child events,
-// see seg_window_len; slot tables of scap points); pairs/pair_vals and their
-// alternates hold pair_cap sort items.
+// see seg_window_len; shared-memory slot tables of scap, then scap_big points,
+// then the global-memory tables gt); pairs/pair_vals and their alternates hold
+// pair_cap sort items.
 void launch_seg_level(const Points &pts, const Span &sp, int level, PassBufs *passes, SegBufs *sbufs, uint64_t *pairs,
                       uint32_t *pair_vals, uint64_t *pairs_alt, uint32_t *vals_alt, unsigned long long *npairs,
                       int *overflow, int64_t pair_cap, int64_t S_cap, int64_t M_cap, int K, int Kmin, int scap,
-                      int min_events, const SortScratch &ss, int32_t *status, cudaStream_t st, int64_t *launches);
+                      int scap_big, int min_events, const SortScratch &ss, const SegTables &gt, int32_t *status,
+                      cudaStream_t st, int64_t *launches);
 
 // Faces of the root movies of both passes (level L = ceil(log2 n) in buffer L & 1):
 // orient, rotate min-first, build the sort key (f0 << 28 | f1) and value f2.

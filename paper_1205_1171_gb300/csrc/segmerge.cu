@@ -20,6 +20,14 @@ struct SegArgs {
     // device work lists (entries: pass << 31 | index)
     unsigned *wlist, *flist, *mlist;  // windows, windows to retry, merges in windows
     int *wcount, *fcount;
+    // windows too large for the biggest shared-memory table: a third round
+    // with per-CTA slot tables of gcap slots in global memory (gtab, gstride
+    // bytes apart); none when gtab is null
+    unsigned *glist;
+    int *gcount;
+    char *gtab;
+    int64_t gstride;
+    int gcap;
     int64_t S_cap, M_cap;
     int32_t *status;
 };
@@ -241,7 +249,6 @@ struct SegIn {
 };
 
 constexpr int SEG_THREADS = 32;
-constexpr int SEG_SLOTS_BIG = 6144;  // retry table (about 170 KB of shared memory)
 
 // first index in [0, cnt) of keys >= key
 __device__ __forceinline__ int64_t lower_key(const uint64_t *keys, int64_t cnt, uint64_t key)
@@ -254,17 +261,18 @@ __device__ __forceinline__ int64_t lower_key(const uint64_t *keys, int64_t cnt, 
     return lo;
 }
 
-// retry = 0: every window, slot table of geo.scap; a window that does not fit
-// marks itself with ocnt = -1.  retry = 1: only those windows, with a table of
-// scap_big; a window that still does not fit sends its merge to the serial
-// fallback.
+// retry = 0: every window, slot table of geo.scap in shared memory; a window
+// that does not fit goes to the retry list.  retry = 1: those windows, with a
+// shared-memory table of scap_big; retry = 2: the ones that still did not
+// fit, with a table of gcap slots in global memory.  A window that fits none
+// sends its merge to the serial fallback.
 __device__ void seg_window(const SegArgs &a, int pass, int64_t g, int retry, int scap_big);
 
 __global__ void __launch_bounds__(SEG_THREADS) k_seg_merge(SegArgs a, int retry, int scap_big)
 {
     if (*a.status) return;
-    const unsigned *list = retry ? a.flist : a.wlist;
-    const int cnt = retry ? *a.fcount : *a.wcount;
+    const unsigned *list = retry == 2 ? a.glist : retry ? a.flist : a.wlist;
+    const int cnt = retry == 2 ? *a.gcount : retry ? *a.fcount : *a.wcount;
     for (int it = blockIdx.x; it < cnt; it += gridDim.x) {
         const unsigned e = list[it];
         seg_window(a, (int)(e >> 31), (int64_t)(e & 0x7fffffffu), retry, scap_big);
@@ -293,7 +301,7 @@ __device__ void seg_window(const SegArgs &a, int pass, int64_t g, int retry, int
     const int S = sb.nseg[m];
     if (s >= S) return;
     if (*a.overflow) { if (threadIdx.x == 0) sb.nofit[m] = 1; return; }
-    const int scap = retry ? scap_big : G.scap;
+    const int scap = retry == 2 ? a.gcap : retry ? scap_big : G.scap;
     const int tid = threadIdx.x;
     const int src = (G.level - 1) & 1;
     const int nl = pb.cnt[src][lo], nr = pb.cnt[src][mid];
@@ -326,12 +334,15 @@ __device__ void seg_window(const SegArgs &a, int pass, int64_t g, int retry, int
     }
     if (tsize > scap) {
         if (tid == 0) {
-            if (retry) sb.nofit[m] = 1;
-            else a.flist[atomicAdd(a.fcount, 1)] = ((unsigned)pass << 31) | (unsigned)g;
+            const unsigned e = ((unsigned)pass << 31) | (unsigned)g;
+            if (retry == 0) a.flist[atomicAdd(a.fcount, 1)] = e;
+            else if (retry == 1 && a.gtab) a.glist[atomicAdd(a.gcount, 1)] = e;
+            else sb.nofit[m] = 1;
         }
         return;
     }
-    int4 *sPt = (int4 *)sm;
+    // the slot table: this CTA's region of global memory in the third round
+    int4 *sPt = retry == 2 ? (int4 *)(a.gtab + (int64_t)blockIdx.x * a.gstride) : (int4 *)sm;
     int2 *sLk = (int2 *)(sPt + scap);
     int *sRK = (int *)(sLk + scap);
     unsigned *sIn = (unsigned *)(sRK + scap);  // window movies as slots: left then right
@@ -552,7 +563,8 @@ size_t seg_smem_bytes(int scap, int K) { return (size_t)scap * (sizeof(int4) + s
 void launch_seg_level(const Points &pts, const Span &sp, int level, PassBufs *passes, SegBufs *sbufs, uint64_t *pairs,
                       uint32_t *pair_vals, uint64_t *pairs_alt, uint32_t *vals_alt, unsigned long long *npairs,
                       int *overflow, int64_t pair_cap, int64_t S_cap, int64_t M_cap, int K, int Kmin, int scap,
-                      int min_events, const SortScratch &ss, int32_t *status, cudaStream_t st, int64_t *launches)
+                      int scap_big, int min_events, const SortScratch &ss, const SegTables &gt, int32_t *status,
+                      cudaStream_t st, int64_t *launches)
 {
     SegArgs a;
     a.pts = pts;
@@ -580,11 +592,16 @@ void launch_seg_level(const Points &pts, const Span &sp, int level, PassBufs *pa
     a.nseg_merges = overflow + 1;
     a.wcount = overflow + 2;
     a.fcount = overflow + 3;
+    a.gcount = overflow + 4;
     a.wlist = sbufs[0].wlist;
     a.flist = sbufs[0].flist;
     a.mlist = sbufs[0].mlist;
+    a.glist = sbufs[0].glist;
+    a.gtab = gt.base;
+    a.gstride = gt.stride;
+    a.gcap = gt.cap;
     cudaMemsetAsync(npairs, 0, sizeof(unsigned long long), st);
-    cudaMemsetAsync(overflow, 0, 4 * sizeof(int), st);
+    cudaMemsetAsync(overflow, 0, 5 * sizeof(int), st);
     a.pairs = pairs;
     a.pair_vals = pair_vals;
     k_seg_bounds<<<dim3((unsigned)((G + 127) / 128), 2), 128, 0, st>>>(a);
@@ -606,11 +623,16 @@ void launch_seg_level(const Points &pts, const Span &sp, int level, PassBufs *pa
                                  st, launches);
     a.pairs = which ? pairs_alt : pairs;
     a.pair_vals = which ? vals_alt : pair_vals;
-    // persistent grids over the device work lists
-    const int wg = flat_grid * 2;  // about 8 one-warp CTAs per SM
+    // persistent grids over the device work lists: up to 16 one-warp CTAs per
+    // SM (small tables fit that many; registers allow about 9)
+    const int wg = flat_grid * 4;
     k_seg_merge<<<wg, SEG_THREADS, seg_smem_bytes(scap, K), st>>>(a, 0, scap);
-    k_seg_merge<<<flat_grid / 4 > 0 ? flat_grid / 4 : 1, SEG_THREADS, seg_smem_bytes(SEG_SLOTS_BIG, K), st>>>(
-        a, 1, SEG_SLOTS_BIG);
+    k_seg_merge<<<flat_grid / 4 > 0 ? flat_grid / 4 : 1, SEG_THREADS, seg_smem_bytes(scap_big, K), st>>>(
+        a, 1, scap_big);
+    if (gt.base) {
+        k_seg_merge<<<gt.ctas, SEG_THREADS, 0, st>>>(a, 2, gt.cap);
+        *launches += 1;
+    }
     k_seg_concat<<<flat_grid, CAT_THREADS, 0, st>>>(a);
     const int64_t fb_threads = 2 * M;
     k_seg_fallback<<<(unsigned)((fb_threads + 63) / 64), 64, 0, st>>>(a);

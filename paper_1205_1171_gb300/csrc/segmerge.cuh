@@ -23,7 +23,8 @@
 //           for the next level are written in parallel: every insert event
 //           (a, w, b) gives w the links (a, b), and the t = -infinity bridge
 //           (u0, v0) joins the two children's t = -infinity hulls.
-// A merge whose window does not fit the slot table is merged serially.
+// A window too large for the shared-memory slot tables gets a table in global
+// memory; a merge with a window that fits no table is merged serially.
 //
 // The phases are written as functions of (thread, thread count) so that the
 // kernels call them between barriers.
@@ -44,6 +45,7 @@ struct SegBufs {
     int2 *bridge0;          // [M_cap]: t = -inf bridge (u0, v0) as ranks
     int *nofit;             // [M_cap]: 1 when a window did not fit (merge serially)
     unsigned *wlist, *flist, *mlist;  // work lists (pass 0's copy holds both passes): [2 S_cap], [2 S_cap], [2 M_cap]
+    unsigned *glist;                  // [2 S_cap]: windows for the global-memory slot tables
 };
 
 // Geometry of one segment level (shared by both passes).

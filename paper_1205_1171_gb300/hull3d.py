@@ -53,11 +53,11 @@ class Hull3DError(RuntimeError):
 
 OPT_NAMES = ("fused_levels", "seg_level", "seg_events", "use_graph", "level_occupancy", "cmp_level", "cmp_slots",
              "seg_slots", "seg_min_events", "merge_order", "seg_events_min", "batch_warp_nodes", "multi_ranks",
-             "float32_ablation")
+             "float32_ablation", "seg_slots_big")
 
 
 class Opts(ctypes.Structure):
-    _fields_ = [(k, ctypes.c_int32) for k in OPT_NAMES] + [("reserved", ctypes.c_int32 * 2)]
+    _fields_ = [(k, ctypes.c_int32) for k in OPT_NAMES] + [("reserved", ctypes.c_int32 * 1)]
 
 
 def load():

@@ -10,7 +10,7 @@ sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
 
-def test_traffic_only_for_the_captured_workload():
+def test_traffic_only_for_the_captured_workload_and_plan():
     t = bench.kernel_traffic()
     if bench.KERNEL_TRAFFIC["sources_sha256"] == bench.sources_sha256():
         assert t == bench.KERNEL_TRAFFIC["bytes_per_launch"]
@@ -18,7 +18,8 @@ def test_traffic_only_for_the_captured_workload():
         assert t is None
     assert bench.kernel_traffic(1 << 22) is None
     assert bench.kernel_traffic(1 << 24, ("cube",)) is None
-    assert bench.kernel_traffic(1 << 24, bench.DISTS, default_plan=False) is None
+    assert bench.kernel_traffic(1 << 24, bench.DISTS, {}) is None  # another plan
+    assert bench.kernel_traffic(1 << 24, bench.DISTS, dict(bench.KERNEL_KNOBS, cmp_level=9)) is None
 
 
 def test_traffic_dropped_when_the_sources_change(monkeypatch):
@@ -39,8 +40,14 @@ def test_issue_roofline_from_the_recorded_counts():
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
     assert 1.0 <= r["active_lanes_per_inst"] <= 32.0
     assert bench.kernel_issue(4.0, 152, 2000.0, 1 << 22) is None
-    assert bench.kernel_issue(4.0, 152, 2000.0, default_plan=False) is None
+    assert bench.kernel_issue(4.0, 152, 2000.0, knobs={}) is None
     assert bench.kernel_issue(0.0, 152, 2000.0) is None
+
+
+def test_the_recorded_knobs_are_the_shipped_tuned_plan():
+    from paper_1205_1171_gb300 import autotune
+
+    assert autotune.lookup("NVIDIA GB300", 1 << 24, path=None, cls="volume") == bench.KERNEL_KNOBS
 
 
 def test_batched_oracle_baseline_on_a_small_batch():

@@ -99,6 +99,21 @@ def test_segment_parallel_levels_agree(H, seg_level, seg_events, seg_slots, seg_
         p.close()
 
 
+@pytest.mark.parametrize("seg_slots_big", [48, 96])
+def test_windows_beyond_the_shared_memory_tables_use_global_tables(H, seg_slots_big):
+    """Windows whose start hulls fit neither shared-memory slot table (both
+    made tiny here) run with slot tables in global memory, with the oracle's
+    faces; hull-heavy clouds (the sphere) put nearly every window there."""
+    p = H.Hull3D(1 << 16, seg_level=8, seg_slots=32, seg_slots_big=seg_slots_big, seg_events=256, seg_events_min=16)
+    try:
+        for dist in inputs.DISTS:
+            for n in (1000, 20000, 1 << 16):
+                pts = inputs.cloud_seeded(dist, n, 5300 + n + seg_slots_big)
+                assert np.array_equal(run(p, pts), oracle.hull(pts)), (dist, n)
+    finally:
+        p.close()
+
+
 @pytest.mark.parametrize("merge_order,occ", [(1, 4), (-1, 4), (1, 3), (1, 1)])
 def test_merge_order_and_register_caps_agree(H, merge_order, occ):
     """Merges of a level run longest first or in x-order, at every register
