@@ -60,13 +60,23 @@ TRAFFIC_SOURCES = ("paper_1205_1171_gb300/csrc/merge.cu", "paper_1205_1171_gb300
 KERNEL_ISSUE = {"warp_inst_per_launch": 1491222985, "thread_inst_per_launch": 16627608858,
                 "sources_sha256": KERNEL_SOURCES_SHA, "knobs": KERNEL_KNOBS}
 ISSUE_PER_SM_PER_CYCLE = 4
+# The batch kernel on the first 4096 clouds of the batch's draw (its four
+# size-class launches, the tuned cut-over), from one ncu capture of
+# `bench.py --batch-only 4096`: DRAM bytes and instructions per cloud, valid
+# for the batch sources and knobs recorded with them; the 65,536-cloud batch
+# is the same draw, so its counts scale with the clouds.
+BATCH_SOURCES = ("paper_1205_1171_gb300/csrc/batch.cu", "paper_1205_1171_gb300/csrc/merge.cuh",
+                 "paper_1205_1171_gb300/csrc/predicates.cuh")
+BATCH_COUNTS = {"clouds": 4096, "dram_bytes": 51715072, "warp_inst": 7291445832, "thread_inst": 84373347737,
+                "knobs": {"batch_warp_nodes": 8},
+                "sources_sha256": "db717640bf938edd2c1fdc446313e06ff74d07f8ceb4dec1e75ed08c46947c8d"}
 
 
-def sources_sha256() -> str:
+def sources_sha256(files=None) -> str:
     import hashlib
 
     h = hashlib.sha256()
-    for rel in TRAFFIC_SOURCES:
+    for rel in files or TRAFFIC_SOURCES:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
@@ -99,6 +109,17 @@ def kernel_issue(ms_per_launch: float, sms: int, sm_mhz: float, npts: int = 1 <<
             "active_lanes_per_inst": KERNEL_ISSUE["thread_inst_per_launch"] / w,
             "peak_basis": f"{ISSUE_PER_SM_PER_CYCLE} warp instructions per SM per cycle x {sms} SMs x "
                           f"{sm_mhz:.0f} MHz (median SM clock of the timed region)"}
+
+
+def batch_counts(knobs, clouds: int):
+    """The recorded batch-kernel counts scaled to `clouds` clouds of the same
+    draw, or None where they do not apply (other knobs or sources)."""
+    rec = BATCH_COUNTS
+    if knobs != rec["knobs"] or rec["sources_sha256"] != sources_sha256(BATCH_SOURCES):
+        return None
+    f = clouds / rec["clouds"]
+    return {"dram_bytes": rec["dram_bytes"] * f, "warp_inst": rec["warp_inst"] * f,
+            "active_lanes_per_inst": rec["thread_inst"] / rec["warp_inst"]}
 
 
 def max_over_ranks(x: float, dist, device: str = "cuda") -> float:
@@ -400,10 +421,20 @@ def batched_leg(hull3d, torch, steps: int, cpu_baseline: bool = False, clouds: i
     total_faces = int(nf.sum().item())
     alg = 12 * len(xyz) + 12 * total_faces  # read every point once, write every face once
     peak, peak_kind = peaks()
+    counts = batch_counts(plan.tuned_knobs, BATCH_CLOUDS)
     roof = {"bound": "hbm", "achieved": alg / (batch_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-            "frac": alg / (batch_ms / 1e3) / 1e9 / peak, "traffic": None, "peak_kind": peak_kind,
-            "kernel": "k_batch (one cloud per CTA from an atomic queue, four size classes)",
+            "frac": alg / (batch_ms / 1e3) / 1e9 / peak, "traffic": counts and counts["dram_bytes"],
+            "peak_kind": peak_kind, "kernel": "k_batch (one cloud per CTA from an atomic queue, four size classes)",
             "alg_bytes_per_batch": alg, "faces": total_faces}
+    if counts:
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        ipk = ISSUE_PER_SM_PER_CYCLE * sms * 2070.0 / 1e3
+        ach = counts["warp_inst"] / (batch_ms / 1e3) / 1e9
+        roof["issue"] = {"bound": "alu", "achieved": ach, "peak": ipk, "unit": "Gwarp-inst/s", "frac": ach / ipk,
+                         "active_lanes_per_inst": counts["active_lanes_per_inst"],
+                         "peak_basis": f"{ISSUE_PER_SM_PER_CYCLE} warp instructions per SM per cycle x {sms} SMs "
+                                       "x 2070 MHz",
+                         "counts": "ncu capture of the first 4096 clouds of the same draw, scaled by the clouds"}
     out = {"workload": "65,536 clouds, sizes round(2^U(4,12)) (16..4096), distribution per cloud uniform over "
                        "cube/ball/sphere/gauss", "points": int(len(xyz)), "roofline": roof,
            "hulls_per_s": BATCH_CLOUDS / (batch_ms / 1e3), "ms_per_batch": batch_ms, "launches_per_batch": launches,

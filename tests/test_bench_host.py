@@ -87,3 +87,15 @@ def test_batch_parity_accepts_the_oracle_faces_and_rejects_a_changed_face():
     with pytest.raises(RuntimeError, match="cloud 5"):
         bench.batch_parity(torch.from_numpy(faces), nt, foff, digests)
     assert bench.batch_parity(ft, nt, foff, {}) == {"clouds": 0, "bit_exact": None}
+
+
+def test_batch_counts_scale_with_the_clouds_and_need_the_recorded_knobs():
+    ok = bench.BATCH_COUNTS["sources_sha256"] == bench.sources_sha256(bench.BATCH_SOURCES)
+    c = bench.batch_counts(bench.BATCH_COUNTS["knobs"], 4 * bench.BATCH_COUNTS["clouds"])
+    if not ok:
+        assert c is None
+        return
+    assert c["warp_inst"] == 4 * bench.BATCH_COUNTS["warp_inst"]
+    assert c["dram_bytes"] == 4 * bench.BATCH_COUNTS["dram_bytes"]
+    assert 1.0 <= c["active_lanes_per_inst"] <= 32.0
+    assert bench.batch_counts({"batch_warp_nodes": 64}, 65536) is None
