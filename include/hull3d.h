@@ -254,13 +254,34 @@ int hull3d_profile(hull3d_plan_t plan, int enable);
 int hull3d_profile_read(hull3d_plan_t plan, double *ms, int64_t *calls);
 
 /* Per merge level launched in global memory: ms[level] summed over the
- * recorded calls (call before hull3d_profile_read, which clears the record). */
+ * recorded calls of hull3d_compute*, hull3d_batch_async and
+ * hull3d_delaunay_async (call before hull3d_profile_read, which clears the
+ * record). */
 int hull3d_profile_levels(hull3d_plan_t plan, double *ms);
 
 /* Movie lengths of the last single-hull call: out[pass * 64 + level] is the
  * total number of events written at that merge level (pass 0 lower, 1
  * upper).  Synchronises the device. */
 int hull3d_level_events(hull3d_plan_t plan, int64_t *out);
+
+/* Time-window counters of the last call (hull3d_compute*, the large clouds of
+ * hull3d_batch_async, hull3d_delaunay_async), both passes together, for the
+ * levels merged in windows (Sec. 3's segment-parallel merge at the top
+ * levels): out[level * HULL3D_WINDOW_STATS + k] with k
+ *   0 the level's start-hull entries overflowed their buffer (1/0: every
+ *     windowed merge of the level then ran serially)
+ *   1 merges cut into windows
+ *   2 windows
+ *   3 windows retried with the larger shared-memory table
+ *   4 windows run with a slot table in global memory
+ *   5 merges that fit no table and ran serially (one thread each)
+ *   6 the window-length multiplier of a second attempt, taken when the
+ *     first one's start-hull entries overflowed (0: none; counters 1-5
+ *     then describe the second attempt)
+ * for level = 0 .. 63 (zero where no windows ran).  out holds
+ * 64 * HULL3D_WINDOW_STATS entries.  Synchronises the device. */
+#define HULL3D_WINDOW_STATS 7
+int hull3d_window_stats(hull3d_plan_t plan, int64_t *out);
 
 #ifdef __cplusplus
 }

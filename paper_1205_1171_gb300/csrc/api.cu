@@ -231,8 +231,8 @@ size_t layout(hull3d_plan_s *p, char *base)
             p->pv0 = b.take<uint32_t>(p->pair_cap);
             p->pv1 = b.take<uint32_t>(p->pair_cap);
             p->npairs = b.take<unsigned long long>(1);
-            // pair overflow, merges in windows, windows, windows to retry, windows for the global tables
-            p->overflow = b.take<int>(5);
+            // per merge level, the window counters (SEG_STAT_STRIDE ints per level)
+            p->overflow = b.take<int>(SEG_STAT_STRIDE * 64);
             // one global-memory slot table per SM for windows whose start hulls exceed the largest shared-memory
             // table (hull-heavy clouds of 2^22 points and more): 32768 slots, windows of up to 4096 child events
             p->gtab.cap = N >= (1 << 20) ? 32768 : 8192;
@@ -442,6 +442,7 @@ int enqueue_levels(hull3d_plan_s *p, const Points &pts, const Span &sp, int ncl,
     // first time-window level (whose kernels read them) and at the roots
     const int ab_level = p->S_cap ? std::min(default_seg_level(p) - 1, L) : L;
     const int LR = ceil_log2(R);
+    if (p->S_cap) CK(cudaMemsetAsync(p->overflow, 0, sizeof(int) * SEG_STAT_STRIDE * 64, st));
     for (int level = l1 + 1; level <= L; level++) {
         // level 2 merges event-free pairs: its own kernel, never time windows
         const bool seg = level >= default_seg_level(p) && p->S_cap && level > 2;
@@ -461,7 +462,8 @@ int enqueue_levels(hull3d_plan_s *p, const Points &pts, const Span &sp, int ncl,
                 *launches += launch_level(pts, sp, level, p->pass, 2, status, st, default_occupancy(p, level), min_ev,
                                           level_order(p, level, &ord), ab_level);
             }
-            launch_seg_level(pts, sp, level, p->pass, p->seg, p->pk0, p->pv0, p->pk1, p->pv1, p->npairs, p->overflow,
+            launch_seg_level(pts, sp, level, p->pass, p->seg, p->pk0, p->pv0, p->pk1, p->pv1, p->npairs,
+                             p->overflow + SEG_STAT_STRIDE * level,
                              p->pair_cap, p->S_cap, p->M_cap, seg_events_at(p, level, lifted), default_seg_events_min(p),
                              seg_slots_at(p, level, lifted), default_seg_slots_big(p), min_ev, p->ss, p->gtab, status,
                              st, launches);
@@ -620,13 +622,10 @@ int enqueue_multi(hull3d_plan_s *p, const int32_t *d_xyz, const int64_t *h_offse
     launch_multi_sort(d_xyz, t, C, total, p->P4, p->k0, p->v0, p->k1, p->v1, p->ss, p->sms, st, launches);
     const Points pts{ p->P4 };
     const Span sp{ R, t.blk, t.cbase, t.cend, t.ctop, t.cstat };
-    // the per-call phase record belongs to single hulls: none is kept here
-    const bool prof = p->profile;
-    p->profile = false;
+    // levels are timed when profiling; the per-call phase record belongs to single hulls
     int slots[HULL3D_PHASES + 1];
     bool seg_marked = false;
     int rc = enqueue_levels(p, pts, sp, C, L, 1, p->status, st, launches, slots, &seg_marked);
-    p->profile = prof;
     if (rc) return rc;
     const int fbits = ceil_log2(nmax);
     launch_multi_faces(pts, t, C, fbits, p->pass, p->k0, p->v0, p->k1, p->v1, 2 * p->max_n, p->ss, p->status,
@@ -652,12 +651,10 @@ int enqueue_delaunay(hull3d_plan_s *p, const int32_t *d_xy, int64_t n, int32_t *
     if (n >= 3) {
         const Points pts{ p->P4 };
         const int L = ceil_log2(n);
-        const bool prof = p->profile;  // the per-call phase record belongs to hulls
-        p->profile = false;
+        // levels are timed when profiling; the per-call phase record belongs to hulls
         int slots[HULL3D_PHASES + 1];
         bool seg_marked = false;
         int rc = enqueue_levels(p, pts, single_span(n), 1, L, 1, status, st, &launches, slots, &seg_marked, true);
-        p->profile = prof;
         if (rc) return rc;
         int fbits = ceil_log2(n);
         if (fbits < 1) fbits = 1;
@@ -1034,6 +1031,19 @@ int hull3d_level_events(hull3d_plan_t p, int64_t *out)
     CK(cudaDeviceSynchronize());
     CK(cudaMemcpy(tmp, p->lev_stats, sizeof tmp, cudaMemcpyDeviceToHost));
     for (int k = 0; k < 128; k++) out[k] = (int64_t)tmp[k];
+    return HULL3D_OK;
+}
+
+int hull3d_window_stats(hull3d_plan_t p, int64_t *out)
+{
+    if (!p || !out) return HULL3D_ERR_INVALID_ARG;
+    for (int k = 0; k < HULL3D_WINDOW_STATS * 64; k++) out[k] = 0;
+    if (!p->overflow) return HULL3D_OK;
+    std::vector<int> tmp(SEG_STAT_STRIDE * 64);
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(tmp.data(), p->overflow, sizeof(int) * tmp.size(), cudaMemcpyDeviceToHost));
+    for (int l = 0; l < 64; l++)
+        for (int k = 0; k < HULL3D_WINDOW_STATS; k++) out[l * HULL3D_WINDOW_STATS + k] = tmp[l * SEG_STAT_STRIDE + k];
     return HULL3D_OK;
 }
 

@@ -25,6 +25,8 @@ struct SegArgs {
     // bytes apart); none when gtab is null
     unsigned *glist;
     int *gcount;
+    int *nserial;  // merges of this level run by the serial fallback
+    int *refit;    // window length multiplier of the second attempt (0: none)
     char *gtab;
     int64_t gstride;
     int gcap;
@@ -33,9 +35,11 @@ struct SegArgs {
 };
 
 // ---- bounds: one thread per (merge, window) --------------------------------
-__global__ void k_seg_bounds(SegArgs a)
+__global__ void k_seg_bounds(SegArgs a, int second)
 {
     if (*a.status) return;
+    const int f = second ? *a.refit : 1;  // the second attempt runs only after a refit
+    if (f <= 1 && second) return;
     const int pass = blockIdx.y;
     const SegGeom &G = a.geo;
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -52,7 +56,9 @@ __global__ void k_seg_bounds(SegArgs a)
     const int src = (G.level - 1) & 1;
     const int nl = pb.cnt[src][lo], nr = pb.cnt[src][mid];
     // small merges are done by the compacted kernel: no windows
-    const int S = (nl + nr > G.min_events) ? seg_count(nl, nr, seg_window_len(nl + nr, G.K, G.Kmin), G.smax) : 0;
+    int len = seg_window_len(nl + nr, G.K, G.Kmin);
+    if (f > 1) len = min(len * f, max(len, SEG_EVCAP_BIG));
+    const int S = (nl + nr > G.min_events) ? seg_count(nl, nr, len, G.smax) : 0;
     if (s == 0) {
         sb.nseg[m] = S;
         sb.nofit[m] = 0;
@@ -152,10 +158,37 @@ __global__ void k_seg_idx(SegArgs a)
 // ---- pairs: each event point joins the start hulls of the windows it spans --
 __device__ void seg_pairs_one(const SegArgs &a, int pass, int64_t q, bool valid);
 
-__global__ void k_seg_pairs(SegArgs a)
+__global__ void k_seg_pairs(SegArgs a, int second)
 {
     if (*a.status) return;
+    if (second && *a.refit <= 1) return;
     for_windowed_events(a, [&](int pass, int64_t q, bool valid) { seg_pairs_one(a, pass, q, valid); });
+}
+
+// ---- refit: longer windows when the start hulls overflowed their buffer --
+// The start-hull entries of a level are (windows) x (child hull sizes).  On
+// the workloads the hulls grow as the square root of the points, but points on
+// a convex surface in lattice order (a planar lattice lifted to the
+// paraboloid: every column of equal x lies on one parabola) keep most of an
+// extreme column on the hull, and the entries can exceed the buffer.  The
+// counter still holds the level's whole demand, so one thread picks the
+// smallest power-of-two multiplier f of the window lengths (at most 64, windows
+// up to SEG_EVCAP_BIG events) that brings the demand under three quarters of
+// the buffer, clears the level's lists, and the bounds and pairs run again
+// with windows f times longer.  The windows that no longer fit the first
+// round's tables take the retry rounds.
+__global__ void k_seg_refit(SegArgs a)
+{
+    if (*a.status || !*a.overflow) return;
+    const unsigned long long demand = *a.npairs;
+    const unsigned long long room = (unsigned long long)(a.geo.pair_cap - a.geo.pair_cap / 4);
+    int f = 2;
+    while (f < 64 && demand > room * (unsigned long long)f) f <<= 1;
+    *a.refit = f;
+    *a.npairs = 0;
+    *a.overflow = 0;
+    *a.nseg_merges = 0;
+    *a.wcount = 0;
 }
 
 __device__ void seg_pairs_one(const SegArgs &a, int pass, int64_t q, bool valid)
@@ -302,6 +335,7 @@ __device__ void seg_window(const SegArgs &a, int pass, int64_t g, int retry, int
     if (s >= S) return;
     if (*a.overflow) { if (threadIdx.x == 0) sb.nofit[m] = 1; return; }
     const int scap = retry == 2 ? a.gcap : retry ? scap_big : G.scap;
+    const int evcap = retry ? SEG_EVCAP_BIG : G.K;  // child events the window's table holds
     const int tid = threadIdx.x;
     const int src = (G.level - 1) & 1;
     const int nl = pb.cnt[src][lo], nr = pb.cnt[src][mid];
@@ -328,11 +362,11 @@ __device__ void seg_window(const SegArgs &a, int pass, int64_t g, int retry, int
     const int nins = s_nins;
     const int base_ins = aL + aR;
     const int tsize = base_ins + nins + 3;  // + the three points of the window's boundary event
-    if (wl + wr > G.K + 1 || aL < 1 || aR < 1) {  // cannot happen for valid movies
+    if (wl + wr > SEG_EVCAP_BIG + 1 || aL < 1 || aR < 1) {  // cannot happen for valid movies
         if (tid == 0) sb.nofit[m] = 1;
         return;
     }
-    if (tsize > scap) {
+    if (tsize > scap || wl + wr > evcap + 1) {
         if (tid == 0) {
             const unsigned e = ((unsigned)pass << 31) | (unsigned)g;
             if (retry == 0) a.flist[atomicAdd(a.fcount, 1)] = e;
@@ -540,6 +574,7 @@ __global__ void k_seg_fallback(SegArgs a)
     if (mid >= hi) return;
     const PassBufs &pb = a.pb[pass];
     if (!a.sb[pass].nofit[m] || a.sb[pass].nseg[m] == 0) return;
+    atomicAdd(a.nserial, 1);
     const int src = (G.level - 1) & 1, dst = G.level & 1;
     GPts gp{ a.pts.P };
     GLinks lk{ pb.lk };
@@ -593,6 +628,8 @@ void launch_seg_level(const Points &pts, const Span &sp, int level, PassBufs *pa
     a.wcount = overflow + 2;
     a.fcount = overflow + 3;
     a.gcount = overflow + 4;
+    a.nserial = overflow + 5;
+    a.refit = overflow + 6;
     a.wlist = sbufs[0].wlist;
     a.flist = sbufs[0].flist;
     a.mlist = sbufs[0].mlist;
@@ -601,10 +638,9 @@ void launch_seg_level(const Points &pts, const Span &sp, int level, PassBufs *pa
     a.gstride = gt.stride;
     a.gcap = gt.cap;
     cudaMemsetAsync(npairs, 0, sizeof(unsigned long long), st);
-    cudaMemsetAsync(overflow, 0, 5 * sizeof(int), st);
     a.pairs = pairs;
     a.pair_vals = pair_vals;
-    k_seg_bounds<<<dim3((unsigned)((G + 127) / 128), 2), 128, 0, st>>>(a);
+    k_seg_bounds<<<dim3((unsigned)((G + 127) / 128), 2), 128, 0, st>>>(a, 0);
     static int flat_grid = 0;
     if (!flat_grid) {
         int dev = 0, sms = 0;
@@ -615,8 +651,12 @@ void launch_seg_level(const Points &pts, const Span &sp, int level, PassBufs *pa
     int64_t fg = (2 * n + 255) / 256;
     if (fg > flat_grid) fg = flat_grid;
     k_seg_idx<<<(unsigned)fg, 256, 0, st>>>(a);
-    k_seg_pairs<<<(unsigned)fg, 256, 0, st>>>(a);
-    *launches += 3;
+    k_seg_pairs<<<(unsigned)fg, 256, 0, st>>>(a, 0);
+    // a second attempt with longer windows, run only when the start hulls overflowed
+    k_seg_refit<<<1, 1, 0, st>>>(a);
+    k_seg_bounds<<<dim3((unsigned)((G + 127) / 128), 2), 128, 0, st>>>(a, 1);
+    k_seg_pairs<<<(unsigned)fg, 256, 0, st>>>(a, 1);
+    *launches += 6;
     int key_bits = 28;
     while ((1ll << (key_bits - 28)) < 4 * S_cap) key_bits++;
     int which = radix_sort_pairs(pairs, pair_vals, pairs_alt, vals_alt, pair_cap, (const int64_t *)npairs, key_bits, ss,
@@ -627,7 +667,7 @@ void launch_seg_level(const Points &pts, const Span &sp, int level, PassBufs *pa
     // SM (small tables fit that many; registers allow about 9)
     const int wg = flat_grid * 4;
     k_seg_merge<<<wg, SEG_THREADS, seg_smem_bytes(scap, K), st>>>(a, 0, scap);
-    k_seg_merge<<<flat_grid / 4 > 0 ? flat_grid / 4 : 1, SEG_THREADS, seg_smem_bytes(scap_big, K), st>>>(
+    k_seg_merge<<<flat_grid / 4 > 0 ? flat_grid / 4 : 1, SEG_THREADS, seg_smem_bytes(scap_big, SEG_EVCAP_BIG), st>>>(
         a, 1, scap_big);
     if (gt.base) {
         k_seg_merge<<<gt.ctas, SEG_THREADS, 0, st>>>(a, 2, gt.cap);

@@ -60,6 +60,17 @@ struct SegGeom {
     int min_events;  // merges with at most this many child events are not merged here
 };
 
+// Child events a window of the retry rounds (the large shared-memory table and
+// the global-memory tables) holds; the first round holds the level's longest
+// window K.
+constexpr int SEG_EVCAP_BIG = 4096;
+
+// Per merge level, the window counters (HULL3D_WINDOW_STATS of them; a block
+// of SEG_STAT_STRIDE ints per level): pair overflow, merges in windows,
+// windows, windows to retry, windows for the global tables, merges run
+// serially, the refit multiplier.
+constexpr int SEG_STAT_STRIDE = 8;
+
 // Window length of a merge with E child events: 2 sqrt(E) within [Kmin, K].
 // A time window starts from the two child hulls at its first instant (their
 // points become start-hull entries), so its setup grows with the hull size

@@ -36,8 +36,9 @@ EXPORTS = (
     "hull3d_plan", "hull3d_plan_opts", "hull3d_destroy", "hull3d_plan_bytes", "hull3d_compute_async", "hull3d_compute",
     "hull3d_compute_host", "hull3d_batch_async", "hull3d_strerror", "hull3d_last_cuda_error",
     "hull3d_last_launch_count", "hull3d_compute_static", "hull3d_profile", "hull3d_profile_read", "hull3d_profile_levels",
-    "hull3d_level_events", "hull3d_adjacency_async", "hull3d_delaunay_async",
+    "hull3d_level_events", "hull3d_adjacency_async", "hull3d_delaunay_async", "hull3d_window_stats",
 )
+WINDOW_STATS = ("pair_overflow", "merges", "windows", "retried", "global_tables", "serial", "refit")
 PHASES = ("sort", "fused", "levels", "seg", "faces")
 
 
@@ -105,6 +106,8 @@ def load():
             lib.hull3d_profile_levels.restype = ctypes.c_int
             lib.hull3d_level_events.argtypes = [P, ctypes.POINTER(i64)]
             lib.hull3d_level_events.restype = ctypes.c_int
+            lib.hull3d_window_stats.argtypes = [P, ctypes.POINTER(i64)]
+            lib.hull3d_window_stats.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -228,6 +231,15 @@ class Hull3D:
         if rc:
             raise Hull3DError(rc, "level_events")
         return np.array(out[:], dtype=np.int64).reshape(2, 64)
+
+    def window_stats(self) -> np.ndarray:
+        """(64, 7) time-window counters per merge level of the last call,
+        columns named by WINDOW_STATS."""
+        out = (ctypes.c_int64 * (64 * len(WINDOW_STATS)))()
+        rc = self._lib.hull3d_window_stats(self._plan, out)
+        if rc:
+            raise Hull3DError(rc, "window_stats")
+        return np.array(out[:], dtype=np.int64).reshape(64, len(WINDOW_STATS))
 
     def compute(self, xyz, stream=None):
         """Canonical faces (F, 3) int32 on the device of xyz (synchronous)."""

@@ -62,6 +62,28 @@ def test_degenerate_sets(plan):
         _same(plan, P.astype(np.int32))
 
 
+def test_tall_lattice_refits_the_windows(H):
+    """A lattice of eight tall columns: lifted to the paraboloid, each
+    column's points lie on one parabola and most of an outer column stays on
+    its child's hull, so the time windows' start hulls overflow their buffer
+    in a plan sized to the input; the windows are cut again, longer, and the
+    triangles still match the oracle's."""
+    n = 8 * 2048
+    xs, ys = np.meshgrid(np.arange(-14000, 14001, 4000), np.arange(-1024, 1024), indexing="ij")
+    pts = np.stack([xs.ravel(), ys.ravel()], 1).astype(np.int32)
+    pts = pts[np.random.default_rng(5).permutation(n)]
+    p = H.Hull3D(n)
+    try:
+        _same(p, pts)
+        ws = p.window_stats()
+        col = {k: i for i, k in enumerate(H.WINDOW_STATS)}
+        refit = ws[:, col["refit"]]
+        assert refit.max() >= 2, ws[9:15].tolist()
+        assert (ws[refit > 0, col["pair_overflow"]] == 0).all(), ws[9:15].tolist()
+    finally:
+        p.close()
+
+
 def test_input_errors(H, plan):
     far = inputs.planar_seeded("square", 1000, 1).copy()
     far[5, 0] = 1 << 15

@@ -103,13 +103,46 @@ def test_segment_parallel_levels_agree(H, seg_level, seg_events, seg_slots, seg_
 def test_windows_beyond_the_shared_memory_tables_use_global_tables(H, seg_slots_big):
     """Windows whose start hulls fit neither shared-memory slot table (both
     made tiny here) run with slot tables in global memory, with the oracle's
-    faces; hull-heavy clouds (the sphere) put nearly every window there."""
+    faces; hull-heavy clouds (the sphere) put nearly every window there.
+    The window counters say where each window ran."""
     p = H.Hull3D(1 << 16, seg_level=8, seg_slots=32, seg_slots_big=seg_slots_big, seg_events=256, seg_events_min=16)
+    col = {k: i for i, k in enumerate(H.WINDOW_STATS)}
     try:
         for dist in inputs.DISTS:
             for n in (1000, 20000, 1 << 16):
                 pts = inputs.cloud_seeded(dist, n, 5300 + n + seg_slots_big)
                 assert np.array_equal(run(p, pts), oracle.hull(pts)), (dist, n)
+                ws = p.window_stats()
+                assert ws[:8].sum() == 0 and ws[17:].sum() == 0, (dist, n)
+                windowed = ws[:, col["windows"]].sum()
+                if n == 1 << 16:
+                    assert windowed > 0 and ws[:, col["merges"]].sum() > 0, (dist, n)
+                    assert ws[:, col["pair_overflow"]].sum() == 0 and ws[:, col["serial"]].sum() == 0, (dist, n)
+                    assert (ws[:, col["global_tables"]] <= ws[:, col["retried"]]).all()
+                    assert (ws[:, col["retried"]] <= ws[:, col["windows"]]).all()
+                    if dist == "sphere":
+                        assert ws[:, col["global_tables"]].sum() > 0, ws[8:17].tolist()
+    finally:
+        p.close()
+
+
+def test_paraboloid_lattice_refits_the_windows(H):
+    """Points of a lattice of eight columns on the paraboloid z = x^2 + y^2:
+    most of an outer column stays on its child's hull, the time windows'
+    start hulls overflow their buffer in a plan sized to the cloud, and the
+    level's windows are cut again, longer, with the oracle's faces."""
+    xs, ys = np.meshgrid(np.arange(-700, 701, 200), np.arange(-512, 512), indexing="ij")
+    x, y = xs.ravel().astype(np.int64), ys.ravel().astype(np.int64)
+    pts = np.stack([x, y, x * x + y * y], 1).astype(np.int32)
+    pts = pts[np.random.default_rng(6).permutation(len(pts))]
+    p = H.Hull3D(len(pts))
+    try:
+        assert np.array_equal(run(p, pts), oracle.hull(pts))
+        ws = p.window_stats()
+        col = {k: i for i, k in enumerate(H.WINDOW_STATS)}
+        refit = ws[:, col["refit"]]
+        assert refit.max() >= 2, ws[9:14].tolist()
+        assert (ws[refit > 0, col["pair_overflow"]] == 0).all(), ws[9:14].tolist()
     finally:
         p.close()
 
