@@ -87,7 +87,9 @@ typedef struct {
                                  and is the only knob here that can change it.  0: exact (default) */
     int32_t seg_slots_big;   /* shared-memory table size of the second round of time windows (<= 6144, automatic:
                                 6144); windows too large for it get slot tables in global memory */
-    int32_t reserved[1];
+    int32_t filter_level;    /* first merge level of the thread-per-merge kernel whose time comparisons try a
+                                float filter before the exact products (the result is the same; automatic: 3 up
+                                to 2^21 points, log2(n) - 15 above, where points share x-values) */
 } hull3d_opts;
 
 /* Creates a plan for hulls of up to max_n points (hull3d_compute*) and for

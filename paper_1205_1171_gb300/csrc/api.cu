@@ -410,6 +410,20 @@ int64_t default_multi_ranks(const hull3d_plan_s *p)
     return (p->opts.multi_ranks > 0 && p->opts.multi_ranks < p->max_n) ? p->opts.multi_ranks : p->max_n;
 }
 
+// First level of the thread-per-merge kernel whose time comparisons try the
+// float filter, for clouds of up to 2^L points.  A cloud spanning the
+// coordinate range has 2^21 x-values (2^16 for lifted planar points); with
+// several points per x-value the low levels' triples through equal-x points
+// tie in Z/Y, where the filter only adds work (at 2^24 points, eight per
+// x-value, it cost 2-4% at levels 2-6 and gained from level 9 on; at 2^20 it
+// gained from level 4).
+int default_filter_level(const hull3d_plan_s *p, int L, bool lifted)
+{
+    if (p->opts.filter_level > 0) return p->opts.filter_level;
+    const int xbits = lifted ? 16 : 21;
+    return L > xbits ? std::max(3, L - xbits + 6) : 3;
+}
+
 // Records a phase-boundary event when profiling (one per boundary per call).
 int mark(hull3d_plan_s *p, cudaStream_t st, int *slot)
 {
@@ -442,6 +456,7 @@ int enqueue_levels(hull3d_plan_s *p, const Points &pts, const Span &sp, int ncl,
     // first time-window level (whose kernels read them) and at the roots
     const int ab_level = p->S_cap ? std::min(default_seg_level(p) - 1, L) : L;
     const int LR = ceil_log2(R);
+    const int filter_from = default_filter_level(p, L, lifted);
     if (p->S_cap) CK(cudaMemsetAsync(p->overflow, 0, sizeof(int) * SEG_STAT_STRIDE * 64, st));
     for (int level = l1 + 1; level <= L; level++) {
         // level 2 merges event-free pairs: its own kernel, never time windows
@@ -460,7 +475,7 @@ int enqueue_levels(hull3d_plan_s *p, const Points &pts, const Span &sp, int ncl,
                 *launches += 1;
             } else {
                 *launches += launch_level(pts, sp, level, p->pass, 2, status, st, default_occupancy(p, level), min_ev,
-                                          level_order(p, level, &ord), ab_level);
+                                          level_order(p, level, &ord), ab_level, level >= filter_from);
             }
             launch_seg_level(pts, sp, level, p->pass, p->seg, p->pk0, p->pv0, p->pk1, p->pv1, p->npairs,
                              p->overflow + SEG_STAT_STRIDE * level,
@@ -472,7 +487,7 @@ int enqueue_levels(hull3d_plan_s *p, const Points &pts, const Span &sp, int ncl,
             *launches += 1;
         } else {
             *launches += launch_level(pts, sp, level, p->pass, 2, status, st, default_occupancy(p, level), -1,
-                                      level_order(p, level, &ord), ab_level);
+                                      level_order(p, level, &ord), ab_level, level >= filter_from);
         }
         if (level > 2) *launches += launch_passthrough(sp, ncl, level, p->pass, status, st);
         if (p->profile) {
@@ -731,7 +746,7 @@ int hull3d_plan(hull3d_plan_t *out, int64_t max_n, int64_t max_clouds, const hul
     if (opts) p->opts = *opts;
     if (p->opts.float32_ablation < 0 || p->opts.float32_ablation > 1 || p->opts.fused_levels < 0 ||
         p->opts.fused_levels > 10 || p->opts.cmp_slots < 0 || p->opts.cmp_slots > 4096 || p->opts.seg_slots_big < 0 ||
-        p->opts.seg_slots_big > 6144 ||
+        p->opts.seg_slots_big > 6144 || p->opts.filter_level < 0 ||
         p->opts.seg_slots < 0 || p->opts.seg_slots > 6144 || p->opts.seg_events < 0 || p->opts.seg_events > 4096 ||
         p->opts.seg_events_min < 0) {
         delete p;
@@ -791,6 +806,7 @@ int hull3d_plan_opts(hull3d_plan_t p, hull3d_opts *out)
     out->seg_events_min = default_seg_events_min(p);
     out->seg_slots = default_seg_slots(p);
     out->seg_slots_big = default_seg_slots_big(p);
+    out->filter_level = default_filter_level(p, ceil_log2(p->max_n), false);
     out->seg_min_events = default_seg_min_events(p);
     out->merge_order = p->opts.merge_order < 0 ? -1 : 1;
     out->batch_warp_nodes = default_batch_warp_nodes(p);

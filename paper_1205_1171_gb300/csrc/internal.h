@@ -85,7 +85,7 @@ struct LevelOrder {
 // number of kernel launches.
 int launch_level(const Points &pts, const Span &sp, int level, PassBufs *passes, int npass, int32_t *status,
                  cudaStream_t st, int occupancy, int max_events = -1, const LevelOrder *ord = nullptr,
-                 int ab_level = 0);
+                 int ab_level = 0, bool filter = true);
 
 // One level (>= 2), one warp per merge on a compacted shared-memory table of
 // up to scap slots (merges that do not fit run the global-memory merge).

@@ -9,6 +9,8 @@
 // movie occupies entries [2 lo, 2 lo + 2 m) of buffer (l & 1) (the paper's
 // eventListOffset = 2 * leftGroupIndex).  Nodes of one level touch disjoint
 // rank ranges, so the in-place link updates never race.
+#include <type_traits>
+
 #include "internal.h"
 #include "merge.cuh"
 
@@ -58,7 +60,8 @@ __global__ void __launch_bounds__(128) k_level2(Points pts, Span sp, PassBufs p0
         cdst[lo] = 0;
         return;
     }
-    GPts gp{ pts.P };
+    GPtsX gp;  // pairs of equal x are common here: no float filter
+    gp.P = pts.P;
     GLinks lk{ glk };
     const bool keep_ab = 2 >= ab_level || hi == end;
     GEvOut out{ pb.W[0] + 2 * lo, keep_ab ? pb.A[0] + 2 * lo : nullptr, keep_ab ? pb.B[0] + 2 * lo : nullptr };
@@ -108,7 +111,7 @@ __global__ void k_order_keys(Span sp, int level, PassBufs p0, PassBufs p1, int64
 // kernels read them from the children of their merges, the faces from the
 // root movie, and the last node of a level is the one a pass-through copy may
 // carry upwards.
-template <int MINB>
+template <int MINB, bool FILT>
 __global__ void __launch_bounds__(128, MINB) k_level(Points pts, Span sp, int level, PassBufs p0, PassBufs p1,
                                                      int max_events, const uint32_t *order, int64_t entries,
                                                      int ab_level, int32_t *status)
@@ -136,7 +139,8 @@ __global__ void __launch_bounds__(128, MINB) k_level(Points pts, Span sp, int le
     int *Adst = upper ? p1.A[dst] : p0.A[dst], *Bdst = upper ? p1.B[dst] : p0.B[dst];
     int nl = csrc[lo], nr = csrc[mid];
     if (max_events >= 0 && nl + nr > max_events) return;  // left to the time-segment kernels
-    GPts gp{ pts.P };
+    typename std::conditional<FILT, GPts, GPtsX>::type gp;
+    gp.P = pts.P;
     GLinks lk{ upper ? p1.lk : p0.lk };
     GEvIn L{ Wsrc + 2 * lo }, R{ Wsrc + 2 * mid };
     const bool keep_ab = level >= ab_level || hi == end;
@@ -201,7 +205,7 @@ int launch_passthrough(const Span &sp, int ncl, int level, PassBufs *passes, int
 }
 
 int launch_level(const Points &pts, const Span &sp, int level, PassBufs *passes, int npass, int32_t *status,
-                 cudaStream_t st, int occupancy, int max_events, const LevelOrder *ord, int ab_level)
+                 cudaStream_t st, int occupancy, int max_events, const LevelOrder *ord, int ab_level, bool filter)
 {
     int launches = 0;
     const int64_t nodes = (sp.n + (1ll << level) - 1) >> level;
@@ -218,14 +222,25 @@ int launch_level(const Points &pts, const Span &sp, int level, PassBufs *passes,
         order = which ? ord->v1 : ord->v0;
         g = dim3((unsigned)((entries + 127) / 128), 1);
     }
-    const int sm = cand_smem_bytes(128);
+    const int sm = cand_smem_bytes(128, filter);
     const Points &P = pts;
     PassBufs &a = passes[0], &b = passes[npass - 1];
     const int ab = ab_level;
-    if (occupancy >= 4) k_level<4><<<g, 128, sm, st>>>(P, sp, level, a, b, max_events, order, entries, ab, status);
-    else if (occupancy == 3) k_level<3><<<g, 128, sm, st>>>(P, sp, level, a, b, max_events, order, entries, ab, status);
-    else if (occupancy == 2) k_level<2><<<g, 128, sm, st>>>(P, sp, level, a, b, max_events, order, entries, ab, status);
-    else k_level<1><<<g, 128, sm, st>>>(P, sp, level, a, b, max_events, order, entries, ab, status);
+#define LEVEL_ARGS P, sp, level, a, b, max_events, order, entries, ab, status
+    if (occupancy >= 4) {
+        if (filter) k_level<4, true><<<g, 128, sm, st>>>(LEVEL_ARGS);
+        else k_level<4, false><<<g, 128, sm, st>>>(LEVEL_ARGS);
+    } else if (occupancy == 3) {
+        if (filter) k_level<3, true><<<g, 128, sm, st>>>(LEVEL_ARGS);
+        else k_level<3, false><<<g, 128, sm, st>>>(LEVEL_ARGS);
+    } else if (occupancy == 2) {
+        if (filter) k_level<2, true><<<g, 128, sm, st>>>(LEVEL_ARGS);
+        else k_level<2, false><<<g, 128, sm, st>>>(LEVEL_ARGS);
+    } else {
+        if (filter) k_level<1, true><<<g, 128, sm, st>>>(LEVEL_ARGS);
+        else k_level<1, false><<<g, 128, sm, st>>>(LEVEL_ARGS);
+    }
+#undef LEVEL_ARGS
     launches++;
     return launches;
 }

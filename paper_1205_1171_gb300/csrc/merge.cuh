@@ -35,6 +35,24 @@ struct Tri {
     int p, q, r;
     int s;  // 0: a member is NIL (time +inf)
     long long Z, Y, Nx;
+    float tf;  // Z / Y in float (NaN when Y = 0): the filter of tri_cmp
+};
+
+// Filter of the time comparison.  tf = fl(fl(Z) / fl(Y)) with the fast
+// division (__fdividef, at most 2 ulp off for |Y| < 2^126; here |Y| < 2^49):
+// the two conversions round to nearest, so |tf - Z/Y| < 2^-21 |Z/Y|.  When
+// fl(tf_a - tf_b) exceeds 2^-19 (|tf_a| + |tf_b|) the true difference of the
+// times has its sign, and the exact products are not needed; nearer times
+// (and every tie) go to the exact tiers.
+constexpr float TF_MARGIN = 1.0f / 524288.0f;
+
+// Whether the triples of points of type PT carry tf and tri_cmp tries the
+// filter first.  Where most comparisons tie in Z/Y (triples through points of
+// equal x: the lowest merge levels of clouds with several points per x-value)
+// the filter only adds work; a point type opts out by specialising this.
+template <class PT>
+struct TimeFilter {
+    static constexpr bool on = true;
 };
 
 // Whether the predicates for points of type PT are the float32 arithmetic of
@@ -63,6 +81,7 @@ __device__ __forceinline__ void tri_make(const PT &pt, Tri &t, int p, int q, int
         t.s = sgnf(Y);
         t.Z = (long long)__float_as_uint(t.s ? Z / Y : 0.f);
         t.Y = t.Nx = 0;
+        t.tf = __uint_as_float(0x7fc00000u);
         return;
     }
     long long ax = Q.x - P.x, ay = Q.y - P.y, az = Q.z - P.z;
@@ -70,6 +89,7 @@ __device__ __forceinline__ void tri_make(const PT &pt, Tri &t, int p, int q, int
     t.Z = ax * bz - bx * az;
     t.Y = ax * by - bx * ay;
     t.Nx = ay * bz - az * by;
+    if constexpr (TimeFilter<PT>::on) t.tf = t.Y ? __fdividef((float)t.Z, (float)t.Y) : __uint_as_float(0x7fc00000u);
     // sign(Y~) = first nonzero of (N.z, -N.x, -N.y), else the eta tier
     if (t.Y) t.s = sgn64(t.Y);
     else if (t.Nx) t.s = -sgn64(t.Nx);
@@ -98,6 +118,14 @@ __device__ __forceinline__ int tri_cmp(const PT &pt, const Tri &a, const Tri &b,
         const float ta = __uint_as_float((unsigned)a.Z), tb = __uint_as_float((unsigned)b.Z);
         s = (ta > tb) - (ta < tb);
         return upper ? -s : s;
+    }
+    if constexpr (TimeFilter<PT>::on) {
+        // both Y nonzero: sign(D0) a.s b.s is the sign of Z_a/Y_a - Z_b/Y_b
+        const float df = a.tf - b.tf;
+        if (fabsf(df) > TF_MARGIN * (fabsf(a.tf) + fabsf(b.tf))) {  // false for NaN
+            s = df > 0.f ? 1 : -1;
+            return upper ? -s : s;
+        }
     }
     const i128 D0 = (i128)a.Z * b.Y - (i128)b.Z * a.Y;
     if (D0 != 0) s = sgn128(D0) * a.s * b.s;
@@ -259,26 +287,31 @@ __device__ int kinetic_forward(const PT &pt, LK &lk, int &u, int &v, Tri old, bo
 // memory traffic; a shared-memory slice per thread, field-major so that the
 // threads of a warp hit distinct banks, keeps them on chip.
 struct CandSmem {
-    int *I;        // [4][6][T]: p, q, r, s
+    int *I;        // [5][6][T]: p, q, r, s, tf (bits)
     long long *Q;  // [3][6][T]: Z, Y, Nx
     int T, t;
     __device__ __forceinline__ int &fi(int f, int l) const { return I[(f * 6 + l) * T + t]; }
     __device__ __forceinline__ long long &fq(int f, int l) const { return Q[(f * 6 + l) * T + t]; }
+    template <bool TF>
     __device__ __forceinline__ Tri get(int l) const
     {
         Tri x;
         x.p = fi(0, l); x.q = fi(1, l); x.r = fi(2, l); x.s = fi(3, l);
+        if constexpr (TF) x.tf = __int_as_float(fi(4, l));
         x.Z = fq(0, l); x.Y = fq(1, l); x.Nx = fq(2, l);
         return x;
     }
+    template <bool TF>
     __device__ __forceinline__ void set(int l, const Tri &x) const
     {
         fi(0, l) = x.p; fi(1, l) = x.q; fi(2, l) = x.r; fi(3, l) = x.s;
+        if constexpr (TF) fi(4, l) = __float_as_int(x.tf);
         fq(0, l) = x.Z; fq(1, l) = x.Y; fq(2, l) = x.Nx;
     }
 };
-// shared-memory bytes of CandSmem for a CTA of T threads
-constexpr int cand_smem_bytes(int T) { return T * 6 * (4 * 4 + 3 * 8); }
+// shared-memory bytes of CandSmem for a CTA of T threads (tf: with the float
+// filter's field)
+constexpr int cand_smem_bytes(int T, bool tf = true) { return T * 6 * ((tf ? 5 : 4) * 4 + 3 * 8); }
 
 template <class PT, class LK, class EIN, class EOUT>
 __device__ int kinetic_forward_sm(const PT &pt, LK &lk, int &u, int &v, const EIN &L, int nl, const EIN &R, int nr,
@@ -330,7 +363,7 @@ __device__ int kinetic_forward_sm(const PT &pt, LK &lk, int &u, int &v, const EI
             }
             Tri t;
             tri_make(pt, t, tp, tq, tr);
-            c.set(l, t);
+            c.template set<TimeFilter<PT>::on>(l, t);
             // a child's next event changes only right after an event of that
             // child was taken (act rewrites links inside one child only), and
             // a child's movie is in time order: it is always later than the
@@ -343,7 +376,7 @@ __device__ int kinetic_forward_sm(const PT &pt, LK &lk, int &u, int &v, const EI
 #pragma unroll 1
         for (int l = 0; l < 6; l++) {
             if (!((valid >> l) & 1u)) continue;
-            const Tri cl = c.get(l);
+            const Tri cl = c.template get<TimeFilter<PT>::on>(l);
             if (best < 0 || tri_cmp(pt, cl, t, upper) < 0) { best = l; t = cl; }
         }
         if (best < 0) break;
@@ -381,6 +414,7 @@ __device__ __forceinline__ Tri shfl_tri(const Tri &t, int src, unsigned mask = 0
     r.Z = __shfl_sync(mask, t.Z, src);
     r.Y = __shfl_sync(mask, t.Y, src);
     r.Nx = __shfl_sync(mask, t.Nx, src);
+    r.tf = __shfl_sync(mask, t.tf, src);
     return r;
 }
 
@@ -621,6 +655,14 @@ struct GPts {  // rank-ordered points in global memory
         return P3{ p.x, p.y, p.z, p.w, r };
     }
     __device__ __forceinline__ int rk(int r) const { return r; }
+};
+
+// The same points, compared without the float filter.
+struct GPtsX : GPts {
+};
+template <>
+struct TimeFilter<GPtsX> {
+    static constexpr bool on = false;
 };
 
 struct GLinks {

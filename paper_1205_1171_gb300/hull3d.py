@@ -54,11 +54,11 @@ class Hull3DError(RuntimeError):
 
 OPT_NAMES = ("fused_levels", "seg_level", "seg_events", "use_graph", "level_occupancy", "cmp_level", "cmp_slots",
              "seg_slots", "seg_min_events", "merge_order", "seg_events_min", "batch_warp_nodes", "multi_ranks",
-             "float32_ablation", "seg_slots_big")
+             "float32_ablation", "seg_slots_big", "filter_level")
 
 
 class Opts(ctypes.Structure):
-    _fields_ = [(k, ctypes.c_int32) for k in OPT_NAMES] + [("reserved", ctypes.c_int32 * 1)]
+    _fields_ = [(k, ctypes.c_int32) for k in OPT_NAMES]
 
 
 def load():
@@ -188,7 +188,7 @@ class Hull3D:
         rc = self._lib.hull3d_plan_opts(self._plan, ctypes.byref(o))
         if rc:
             raise Hull3DError(rc, "plan_opts")
-        return {k: getattr(o, k) for k, _ in Opts._fields_ if k != "reserved"}
+        return {k: getattr(o, k) for k, _ in Opts._fields_}
 
     @property
     def fused_levels_used(self) -> int:

@@ -20,6 +20,7 @@
 #define __forceinline__ inline
 #define __noinline__
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -44,6 +45,9 @@ static inline float __uint_as_float(unsigned u)
     std::memcpy(&f, &u, sizeof f);
     return f;
 }
+static inline float __int_as_float(int i) { return __uint_as_float((unsigned)i); }
+static inline int __float_as_int(float f) { return (int)__float_as_uint(f); }
+static inline float __fdividef(float a, float b) { return a / b; }
 
 #include "../../paper_1205_1171_gb300/csrc/merge.cuh"
 
@@ -143,7 +147,7 @@ extern "C" int merge_header_hull(const int32_t *xyz, int64_t n, int form, int cm
     std::vector<uint64_t> fk;
     std::vector<int32_t> fv;
     GPts gp{ P.data() };
-    int cand_i[4 * 6];        // CandSmem of one thread: p, q, r, s of six candidates
+    int cand_i[5 * 6];        // CandSmem of one thread: p, q, r, s, tf of six candidates
     long long cand_q[3 * 6];  // and their Z, Y, Nx
     const CandSmem cs{ cand_i, cand_q, 1, 0 };
     for (int pass = 0; pass < 2; pass++) {

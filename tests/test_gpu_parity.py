@@ -163,6 +163,29 @@ def test_merge_order_and_register_caps_agree(H, merge_order, occ):
         p.close()
 
 
+@pytest.mark.parametrize("filter_level", [3, 64])
+def test_float_time_filter_on_and_off_agree(H, filter_level):
+    """The time comparisons' float filter (from level 3) and the exact
+    products alone (never) give the oracle's faces, on clouds with many
+    points per x-value too (where the filter's times tie)."""
+    p = H.Hull3D(1 << 15, filter_level=filter_level)
+    try:
+        for dist in inputs.DISTS:
+            for n in (5, 77, 1000, 1 << 15):
+                pts = inputs.cloud_seeded(dist, n, 8700 + n + filter_level)
+                assert np.array_equal(run(p, pts), oracle.hull(pts)), (dist, n)
+        rng = np.random.default_rng(filter_level)
+        for _ in range(4):  # eight points per x-value, as at 2^24 in the full range
+            pts = np.unique(np.stack([rng.integers(-512, 512, 8192), rng.integers(-(1 << 20), 1 << 20, 8192),
+                                      rng.integers(-(1 << 20), 1 << 20, 8192)], 1), axis=0).astype(np.int32)
+            pts = pts[rng.permutation(len(pts))]
+            assert np.array_equal(run(p, pts), oracle.hull(pts))
+        for pts in _tiny_sets(100, 41):
+            assert np.array_equal(run(p, pts), oracle.hull(pts)), pts.tolist()
+    finally:
+        p.close()
+
+
 def test_config_small_cube_4096(plan):
     pts = inputs.cloud_seeded("cube", 4096, inputs.seed_for(1))
     got = run(plan, pts)
