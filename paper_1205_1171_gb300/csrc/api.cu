@@ -348,9 +348,19 @@ int seg_min_events_at(const hull3d_plan_s *p, int64_t n, int level)
 // 2^24 cube and clipped Gaussian: 3% per hull).  Level 2's merges of
 // event-free pairs are all alike, and from level 9 on there are too few merges
 // for the sort to pay.
-const LevelOrder *level_order(const hull3d_plan_s *p, int level, const LevelOrder *ord)
+const LevelOrder *level_order(const hull3d_plan_s *p, int level, LevelOrder *ord, bool typed)
 {
+    ord->typed = typed;
     return (p->opts.merge_order >= 0 && level >= 3 && level <= 8) ? ord : nullptr;
+}
+// Last level whose merge order groups the merges by how their points share
+// x-values (k_order_keys), for clouds of up to 2^L points: levels up to
+// L - 20 (3 and 4 at 2^24 points, eight per x-value: level 3 8.3 -> 7.8 ms
+// on the cube; from level 5 on the work order alone is faster).
+int default_typed_level(int L, bool lifted)
+{
+    const int xbits = lifted ? 16 : 21;
+    return L - xbits + 1;
 }
 int default_seg_events(const hull3d_plan_s *p) { return p->opts.seg_events > 0 ? p->opts.seg_events : 512; }
 // Longest time window of a level.  A window starts from both child hulls,
@@ -451,7 +461,8 @@ int enqueue_levels(hull3d_plan_s *p, const Points &pts, const Span &sp, int ncl,
                    cudaStream_t st, int64_t *launches, int *slots, bool *seg_marked, bool lifted = false)
 {
     const int64_t R = sp.n;  // the rank space: thresholds follow the merges a level holds
-    const LevelOrder ord{ p->k0, p->k1, p->v0, p->v1, p->ss };
+    LevelOrder ord{ p->k0, p->k1, p->v0, p->v1, p->ss, false };
+    const int typed_to = default_typed_level(L, lifted);
     // parent movies keep their event neighbours from the level below the
     // first time-window level (whose kernels read them) and at the roots
     const int ab_level = p->S_cap ? std::min(default_seg_level(p) - 1, L) : L;
@@ -475,7 +486,8 @@ int enqueue_levels(hull3d_plan_s *p, const Points &pts, const Span &sp, int ncl,
                 *launches += 1;
             } else {
                 *launches += launch_level(pts, sp, level, p->pass, 2, status, st, default_occupancy(p, level), min_ev,
-                                          level_order(p, level, &ord), ab_level, level >= filter_from);
+                                          level_order(p, level, &ord, level <= typed_to), ab_level,
+                                          level >= filter_from);
             }
             launch_seg_level(pts, sp, level, p->pass, p->seg, p->pk0, p->pv0, p->pk1, p->pv1, p->npairs,
                              p->overflow + SEG_STAT_STRIDE * level,
@@ -487,7 +499,8 @@ int enqueue_levels(hull3d_plan_s *p, const Points &pts, const Span &sp, int ncl,
             *launches += 1;
         } else {
             *launches += launch_level(pts, sp, level, p->pass, 2, status, st, default_occupancy(p, level), -1,
-                                      level_order(p, level, &ord), ab_level, level >= filter_from);
+                                      level_order(p, level, &ord, level <= typed_to), ab_level,
+                                          level >= filter_from);
         }
         if (level > 2) *launches += launch_passthrough(sp, ncl, level, p->pass, status, st);
         if (p->profile) {

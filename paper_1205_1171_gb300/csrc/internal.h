@@ -75,6 +75,7 @@ struct LevelOrder {
     uint64_t *k0, *k1;
     uint32_t *v0, *v1;
     SortScratch ss;
+    bool typed;  // group the merges by how their points share x-values first (k_order_keys)
 };
 
 // One level (>= 2), one thread per merge, global memory.  With max_events >= 0

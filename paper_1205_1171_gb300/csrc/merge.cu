@@ -83,9 +83,13 @@ void launch_level2(const Points &pts, const Span &sp, PassBufs *passes, int ab_l
 // child event count, longest first.  In x-order, neighbouring merges take
 // quite different numbers of rounds and a warp runs as long as its longest
 // merge (about 70% of the lanes busy on a uniform cube); sorted, the 32 merges
-// of a warp take about as many rounds each.
-__global__ void k_order_keys(Span sp, int level, PassBufs p0, PassBufs p1, int64_t nodes, uint64_t *keys,
-                             uint32_t *vals)
+// of a warp take about as many rounds each.  With `typed`, merges are first
+// grouped by how their points share x-values (all on one, the two children
+// meeting on one, neither): where most points share x-values with others (the
+// lowest levels of clouds with several points per x-value) the comparisons of
+// such merges take the same tie tiers, so a warp of one kind diverges less.
+__global__ void k_order_keys(Points pts, Span sp, int level, PassBufs p0, PassBufs p1, int64_t nodes, bool typed,
+                             uint64_t *keys, uint32_t *vals)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= 2 * nodes) return;
@@ -94,13 +98,19 @@ __global__ void k_order_keys(Span sp, int level, PassBufs p0, PassBufs p1, int64
     const int src = (level - 1) & 1;
     const int64_t lo = node << level, mid = lo + (1ll << (level - 1));
     unsigned work = 0;  // no node, or one without a right child: sorts last (k_level skips it)
+    unsigned kind = 3;
     int64_t hi;
     if (node_span(sp, level, lo, hi) && mid < hi) {
         const int *c = (pass ? p1 : p0).cnt[src];
         const unsigned w = (unsigned)c[lo] + (unsigned)c[mid];
-        work = (w < 0xfffeu ? w : 0xfffeu) + 1;
+        work = (w < 0x3ffeu ? w : 0x3ffeu) + 1;
+        kind = 0;
+        if (typed) {
+            const int x0 = pts.P[lo].x, x1 = pts.P[hi - 1].x;
+            kind = x0 == x1 ? 0u : (pts.P[mid - 1].x == pts.P[mid].x ? 1u : 2u);
+        }
     }
-    keys[i] = 0xffffu - work;
+    keys[i] = (kind << 14) | (0x3fffu - work);
     vals[i] = ((uint32_t)pass << 31) | (uint32_t)node;
 }
 
@@ -214,8 +224,8 @@ int launch_level(const Points &pts, const Span &sp, int level, PassBufs *passes,
     int64_t entries = 0;
     if (ord && npass == 2) {
         entries = 2 * nodes;
-        k_order_keys<<<(unsigned)((entries + 255) / 256), 256, 0, st>>>(sp, level, passes[0], passes[1], nodes,
-                                                                         ord->k0, ord->v0);
+        k_order_keys<<<(unsigned)((entries + 255) / 256), 256, 0, st>>>(pts, sp, level, passes[0], passes[1], nodes,
+                                                                         ord->typed, ord->k0, ord->v0);
         int64_t sl = 0;
         const int which = radix_sort_pairs(ord->k0, ord->v0, ord->k1, ord->v1, entries, nullptr, 16, ord->ss, st, &sl);
         launches += 1 + (int)sl;
