@@ -84,8 +84,9 @@ void launch_level2(const Points &pts, const Span &sp, PassBufs *passes, int ab_l
 // quite different numbers of rounds and a warp runs as long as its longest
 // merge (about 70% of the lanes busy on a uniform cube); sorted, the 32 merges
 // of a warp take about as many rounds each.  With `typed`, merges are first
-// grouped by how their points share x-values (all on one, the two children
-// meeting on one, neither): where most points share x-values with others (the
+// grouped by how their points share x-values (the x-value changes along the
+// node, up to three, and whether the two children meet on one x-value): where
+// most points share x-values with others (the
 // lowest levels of clouds with several points per x-value) the comparisons of
 // such merges take the same tie tiers, so a warp of one kind diverges less.
 __global__ void k_order_keys(Points pts, Span sp, int level, PassBufs p0, PassBufs p1, int64_t nodes, bool typed,
@@ -98,19 +99,24 @@ __global__ void k_order_keys(Points pts, Span sp, int level, PassBufs p0, PassBu
     const int src = (level - 1) & 1;
     const int64_t lo = node << level, mid = lo + (1ll << (level - 1));
     unsigned work = 0;  // no node, or one without a right child: sorts last (k_level skips it)
-    unsigned kind = 3;
+    unsigned kind = 7;
     int64_t hi;
     if (node_span(sp, level, lo, hi) && mid < hi) {
         const int *c = (pass ? p1 : p0).cnt[src];
         const unsigned w = (unsigned)c[lo] + (unsigned)c[mid];
-        work = (w < 0x3ffeu ? w : 0x3ffeu) + 1;
+        work = (w < 0x1ffeu ? w : 0x1ffeu) + 1;
         kind = 0;
-        if (typed) {
-            const int x0 = pts.P[lo].x, x1 = pts.P[hi - 1].x;
-            kind = x0 == x1 ? 0u : (pts.P[mid - 1].x == pts.P[mid].x ? 1u : 2u);
+        if (typed) {  // x-value changes along the node (at most 3), and whether the children meet on one
+            int changes = 0, xp = pts.P[lo].x;
+            for (int64_t r = lo + 1; r < hi && changes < 3; r++) {
+                const int x = pts.P[r].x;
+                changes += x != xp;
+                xp = x;
+            }
+            kind = (unsigned)changes * 2u + (pts.P[mid - 1].x == pts.P[mid].x ? 0u : 1u);
         }
     }
-    keys[i] = (kind << 14) | (0x3fffu - work);
+    keys[i] = (kind << 13) | (0x1fffu - work);
     vals[i] = ((uint32_t)pass << 31) | (uint32_t)node;
 }
 
