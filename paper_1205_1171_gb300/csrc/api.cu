@@ -355,12 +355,13 @@ const LevelOrder *level_order(const hull3d_plan_s *p, int level, LevelOrder *ord
 }
 // Last level whose merge order groups the merges by how their points share
 // x-values (k_order_keys), for clouds of up to 2^L points: levels up to
-// L - 20 (3 and 4 at 2^24 points, eight per x-value: level 3 8.3 -> 7.8 ms
-// on the cube; from level 5 on the work order alone is faster).
+// L - 19 (3 to 5 at 2^24 points, eight per x-value: levels 3-5 of the cube
+// 19.5 -> 18.6 ms, of the Gaussian 21.5 -> 20.6 ms; at level 6 and above the
+// work order alone is faster).
 int default_typed_level(int L, bool lifted)
 {
     const int xbits = lifted ? 16 : 21;
-    return L - xbits + 1;
+    return L - xbits + 2;
 }
 int default_seg_events(const hull3d_plan_s *p) { return p->opts.seg_events > 0 ? p->opts.seg_events : 512; }
 // Longest time window of a level.  A window starts from both child hulls,
