@@ -52,12 +52,12 @@ def peaks():
 # and the plan knobs that are recorded with them.  The instruction counts give
 # the second roofline: instruction issue, against 4 warp instructions per SM
 # per cycle (one per SM sub-partition).
-KERNEL_SOURCES_SHA = "bcf53818d5f4afdb746838f0454fc5377cdfc83e14b577167c137e10448a94ce"
+KERNEL_SOURCES_SHA = "1ceea4917f2c45dc3880b8cd25640f1441e81c01f8abc74305c0bbef5e001464"
 KERNEL_KNOBS = {"cmp_level": 13, "level_occupancy": 0, "seg_events": 256, "seg_level": 12, "seg_min_events": 0}
-KERNEL_TRAFFIC = {"bytes_per_launch": 2321678208, "sources_sha256": KERNEL_SOURCES_SHA, "knobs": KERNEL_KNOBS}
+KERNEL_TRAFFIC = {"bytes_per_launch": 2329560857, "sources_sha256": KERNEL_SOURCES_SHA, "knobs": KERNEL_KNOBS}
 TRAFFIC_SOURCES = ("paper_1205_1171_gb300/csrc/merge.cu", "paper_1205_1171_gb300/csrc/merge.cuh",
                    "paper_1205_1171_gb300/csrc/predicates.cuh")
-KERNEL_ISSUE = {"warp_inst_per_launch": 1491222985, "thread_inst_per_launch": 16627608858,
+KERNEL_ISSUE = {"warp_inst_per_launch": 1377490529, "thread_inst_per_launch": 16486632619,
                 "sources_sha256": KERNEL_SOURCES_SHA, "knobs": KERNEL_KNOBS}
 ISSUE_PER_SM_PER_CYCLE = 4
 # The batch kernel on the first 4096 clouds of the batch's draw (its four
@@ -67,9 +67,9 @@ ISSUE_PER_SM_PER_CYCLE = 4
 # is the same draw, so its counts scale with the clouds.
 BATCH_SOURCES = ("paper_1205_1171_gb300/csrc/batch.cu", "paper_1205_1171_gb300/csrc/merge.cuh",
                  "paper_1205_1171_gb300/csrc/predicates.cuh")
-BATCH_COUNTS = {"clouds": 4096, "dram_bytes": 51715072, "warp_inst": 7291445832, "thread_inst": 84373347737,
+BATCH_COUNTS = {"clouds": 4096, "dram_bytes": 57661696, "warp_inst": 6419680896, "thread_inst": 78475376327,
                 "knobs": {"batch_warp_nodes": 8},
-                "sources_sha256": "db717640bf938edd2c1fdc446313e06ff74d07f8ceb4dec1e75ed08c46947c8d"}
+                "sources_sha256": "2cc68164bbadcaca5c0ca2b690dfa6fd5eb7591fe848a5b9d8d6cecc3f4f04d0"}
 
 
 def sources_sha256(files=None) -> str:
