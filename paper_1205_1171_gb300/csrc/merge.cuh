@@ -437,19 +437,23 @@ __device__ int kinetic_forward_warp(const PT &pt, LK &lk, int &u, int &v, Tri ol
     int i = 0, j = 0, k = 0;
     for (;;) {
         if (stop_at_end && i >= nl && j >= nr) break;
+        // every lane reads the same few links (broadcast loads, no branch per
+        // candidate), then lane l < 6 picks its triple
+        const int e0 = i < nl ? (int)(L.w(i) & RANK_MASK) : NIL;
+        const int e1 = j < nr ? (int)(R.w(j) & RANK_MASK) : NIL;
+        const int2 lu = lk.get(u), lv = lk.get(v);
+        const int2 l0 = e0 >= 0 ? lk.get(e0) : make_int2(NIL, NIL);
+        const int2 l1 = e1 >= 0 ? lk.get(e1) : make_int2(NIL, NIL);
         if (lane < 6) {
-            int tp = NIL, tq = NIL, tr = NIL;
-            if (lane == 0) {
-                if (i < nl) { tq = (int)(L.w(i) & RANK_MASK); int2 l0 = lk.get(tq); tp = l0.x; tr = l0.y; }
-            } else if (lane == 1) {
-                if (j < nr) { tq = (int)(R.w(j) & RANK_MASK); int2 l1 = lk.get(tq); tp = l1.x; tr = l1.y; }
-            } else if (lane == 2) { tp = u; tq = lk.nxt(u); tr = v; }
-            else if (lane == 3) { tp = lk.prv(u); tq = u; tr = v; }
-            else if (lane == 4) { tp = u; tq = lk.prv(v); tr = v; }
-            else { tp = u; tq = v; tr = lk.nxt(v); }
+            const int tp = lane == 0 ? l0.x : lane == 1 ? l1.x : lane == 3 ? lu.x : u;
+            const int tq = lane == 0 ? e0 : lane == 1 ? e1 : lane == 2 ? lu.y : lane == 3 ? u : lane == 4 ? lv.x : v;
+            const int tr = lane == 0 ? l0.y : lane == 1 ? l1.y : lane == 5 ? lv.y : v;
             if (tp != c.p || tq != c.q || tr != c.r) {
                 tri_make(pt, c, tp, tq, tr);
-                valid = c.s != 0 && (!have_old || tri_cmp(pt, c, old, upper) > 0);
+                // a child's next event is always later than the last event
+                // (its movie is in time order and it changes only after one of
+                // its events was taken): only the bridge moves are compared
+                valid = c.s != 0 && (lane <= 1 || !have_old || tri_cmp(pt, c, old, upper) > 0);
             }
         }
         // all 15 pairs at once: lane k < 15 compares candidates (i, j) = pair k;
