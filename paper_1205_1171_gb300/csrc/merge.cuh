@@ -462,9 +462,26 @@ __device__ int kinetic_forward_warp(const PT &pt, LK &lk, int &u, int &v, Tri ol
         const int pk = lane < 15 ? lane : 0;
         const int pi = pk < 5 ? 0 : pk < 9 ? 1 : pk < 12 ? 2 : pk < 14 ? 3 : 4;
         const int pj = pk - (pi == 0 ? -1 : pi == 1 ? 3 : pi == 2 ? 6 : pi == 3 ? 8 : 9);
-        const Tri ti = shfl_tri(c, pi), tj = shfl_tri(c, pj);
         const bool vi = __shfl_sync(FULL, valid, pi) != 0, vj = __shfl_sync(FULL, valid, pj) != 0;
-        const bool ibeats = lane < 15 && vi && (!vj || tri_cmp(pt, ti, tj, upper) <= 0);
+        bool ibeats;
+        if constexpr (TimeFilter<PT>::on) {
+            // the float times first; the whole triples move only when some
+            // pair is too close for them to decide
+            const float fi = __shfl_sync(FULL, c.tf, pi), fj = __shfl_sync(FULL, c.tf, pj);
+            const float df = fi - fj;
+            int dec = fabsf(df) > TF_MARGIN * (fabsf(fi) + fabsf(fj)) ? (df > 0.f ? 1 : -1) : 0;  // 0: NaN or near
+            if (upper) dec = -dec;
+            const bool both = lane < 15 && vi && vj;
+            if (__any_sync(FULL, both && dec == 0)) {
+                const Tri ti = shfl_tri(c, pi), tj = shfl_tri(c, pj);
+                ibeats = lane < 15 && vi && (!vj || (dec != 0 ? dec < 0 : tri_cmp(pt, ti, tj, upper) <= 0));
+            } else {
+                ibeats = lane < 15 && vi && (!vj || dec < 0);
+            }
+        } else {
+            const Tri ti = shfl_tri(c, pi), tj = shfl_tri(c, pj);
+            ibeats = lane < 15 && vi && (!vj || tri_cmp(pt, ti, tj, upper) <= 0);
+        }
         const unsigned win = __ballot_sync(FULL, ibeats);
         const unsigned vmask = __ballot_sync(FULL, lane < 6 && valid) & 0x3fu;
         int best = -1;
