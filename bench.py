@@ -53,7 +53,7 @@ def peaks():
 # the second roofline: instruction issue, against 4 warp instructions per SM
 # per cycle (one per SM sub-partition).
 KERNEL_SOURCES_SHA = "1ceea4917f2c45dc3880b8cd25640f1441e81c01f8abc74305c0bbef5e001464"
-KERNEL_KNOBS = {"cmp_level": 13, "level_occupancy": 0, "seg_events": 256, "seg_level": 12, "seg_min_events": 0}
+KERNEL_KNOBS = {"cmp_level": 12, "level_occupancy": 0, "seg_events": 256, "seg_level": 12, "seg_min_events": 0}
 KERNEL_TRAFFIC = {"bytes_per_launch": 2329560857, "sources_sha256": KERNEL_SOURCES_SHA, "knobs": KERNEL_KNOBS}
 TRAFFIC_SOURCES = ("paper_1205_1171_gb300/csrc/merge.cu", "paper_1205_1171_gb300/csrc/merge.cuh",
                    "paper_1205_1171_gb300/csrc/predicates.cuh")
@@ -68,7 +68,7 @@ ISSUE_PER_SM_PER_CYCLE = 4
 BATCH_SOURCES = ("paper_1205_1171_gb300/csrc/batch.cu", "paper_1205_1171_gb300/csrc/merge.cuh",
                  "paper_1205_1171_gb300/csrc/predicates.cuh")
 BATCH_COUNTS = {"clouds": 4096, "dram_bytes": 57661696, "warp_inst": 6419680896, "thread_inst": 78475376327,
-                "knobs": {"batch_warp_nodes": 8},
+                "knobs": {"batch_warp_nodes": 16},
                 "sources_sha256": "2cc68164bbadcaca5c0ca2b690dfa6fd5eb7591fe848a5b9d8d6cecc3f4f04d0"}
 
 
