@@ -46,18 +46,18 @@ def peaks():
 
 
 # DRAM bytes (read + write) and instructions per launch of the thread-per-merge
-# level kernel (levels 3-12 of the two n = 2^24 clouds, 20 launches, averaged),
+# level kernel (levels 3-11 of the two n = 2^24 clouds, 18 launches, averaged),
 # from one-pass ncu captures of `bench.py --profile-once` (the command and the
 # per-level figures are in profiles/), valid for the merge sources whose SHA-256
 # and the plan knobs that are recorded with them.  The instruction counts give
 # the second roofline: instruction issue, against 4 warp instructions per SM
 # per cycle (one per SM sub-partition).
-KERNEL_SOURCES_SHA = "1ceea4917f2c45dc3880b8cd25640f1441e81c01f8abc74305c0bbef5e001464"
+KERNEL_SOURCES_SHA = "f23555662a8a0d1d15883a65d3c4324d3907c14d68a693f6d8a5b078f1c8ded2"
 KERNEL_KNOBS = {"cmp_level": 12, "level_occupancy": 0, "seg_events": 256, "seg_level": 12, "seg_min_events": 0}
-KERNEL_TRAFFIC = {"bytes_per_launch": 2329560857, "sources_sha256": KERNEL_SOURCES_SHA, "knobs": KERNEL_KNOBS}
+KERNEL_TRAFFIC = {"bytes_per_launch": 2578944028, "sources_sha256": KERNEL_SOURCES_SHA, "knobs": KERNEL_KNOBS}
 TRAFFIC_SOURCES = ("paper_1205_1171_gb300/csrc/merge.cu", "paper_1205_1171_gb300/csrc/merge.cuh",
                    "paper_1205_1171_gb300/csrc/predicates.cuh")
-KERNEL_ISSUE = {"warp_inst_per_launch": 1377490529, "thread_inst_per_launch": 16486632619,
+KERNEL_ISSUE = {"warp_inst_per_launch": 1523402311, "thread_inst_per_launch": 18230573092,
                 "sources_sha256": KERNEL_SOURCES_SHA, "knobs": KERNEL_KNOBS}
 ISSUE_PER_SM_PER_CYCLE = 4
 # The batch kernel on the first 4096 clouds of the batch's draw (its four
@@ -67,9 +67,9 @@ ISSUE_PER_SM_PER_CYCLE = 4
 # is the same draw, so its counts scale with the clouds.
 BATCH_SOURCES = ("paper_1205_1171_gb300/csrc/batch.cu", "paper_1205_1171_gb300/csrc/merge.cuh",
                  "paper_1205_1171_gb300/csrc/predicates.cuh")
-BATCH_COUNTS = {"clouds": 4096, "dram_bytes": 57661696, "warp_inst": 6419680896, "thread_inst": 78475376327,
+BATCH_COUNTS = {"clouds": 4096, "dram_bytes": 58100992, "warp_inst": 7451539633, "thread_inst": 117389443396,
                 "knobs": {"batch_warp_nodes": 16},
-                "sources_sha256": "2cc68164bbadcaca5c0ca2b690dfa6fd5eb7591fe848a5b9d8d6cecc3f4f04d0"}
+                "sources_sha256": "dfee9df38b6d97f09c7af2ac2f1d1b4df639ee77aa0c934d35dfab745aac0527"}
 
 
 def sources_sha256(files=None) -> str:
