@@ -53,7 +53,10 @@ def peaks():
 # the second roofline: instruction issue, against 4 warp instructions per SM
 # per cycle (one per SM sub-partition).
 KERNEL_SOURCES_SHA = "f23555662a8a0d1d15883a65d3c4324d3907c14d68a693f6d8a5b078f1c8ded2"
-KERNEL_KNOBS = {"cmp_level": 12, "level_occupancy": 0, "seg_events": 256, "seg_level": 12, "seg_min_events": 0}
+# (the shortest time window, seg_events_min, acts only from the first time-window
+# level, 12, above every level the counted kernel runs, 3-11)
+KERNEL_KNOBS = {"cmp_level": 12, "level_occupancy": 0, "seg_events": 256, "seg_level": 12, "seg_min_events": 0,
+                "seg_events_min": 64}
 KERNEL_TRAFFIC = {"bytes_per_launch": 2578944028, "sources_sha256": KERNEL_SOURCES_SHA, "knobs": KERNEL_KNOBS}
 TRAFFIC_SOURCES = ("paper_1205_1171_gb300/csrc/merge.cu", "paper_1205_1171_gb300/csrc/merge.cuh",
                    "paper_1205_1171_gb300/csrc/predicates.cuh")

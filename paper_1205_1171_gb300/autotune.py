@@ -35,7 +35,7 @@ from typing import Callable, Iterable
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_CACHE = os.path.join(HERE, "_build", "tuning.json")
 SHIPPED_CACHE = os.path.join(HERE, "tuning_gb300.json")
-KNOBS = ("cmp_level", "seg_level", "seg_events", "seg_min_events", "level_occupancy")
+KNOBS = ("cmp_level", "seg_level", "seg_events", "seg_min_events", "level_occupancy", "seg_events_min")
 KIND_KNOBS = {"single": KNOBS, "multi": KNOBS + ("multi_ranks",), "batch": ("batch_warp_nodes",)}
 CLASSES = {"volume": ("cube", "ball", "gauss"), "surface": ("sphere",)}
 
@@ -58,11 +58,13 @@ def candidates(n: int) -> list[dict]:
     cmp_levels = sorted({0} | {min(L + 1, c) for c in (max(6, L - 12), max(6, L - 10), 13)}
                         | ({3, 4} if L <= 16 else set()))  # small hulls: the warp kernel from low levels
     seg_levels = sorted({min(L + 1, s) for s in (8, 10, 12, 64)})
-    out = [dict(cmp_level=0, seg_level=0, seg_events=0, seg_min_events=0, level_occupancy=0)]  # the defaults
-    for cl, sl, K, smin, occ in itertools.product(cmp_levels, seg_levels, (256, 512, 1024), (0, 256, 512), (0, 4)):
-        if sl > L and (K != 512 or smin != 0):
+    out = [dict(cmp_level=0, seg_level=0, seg_events=0, seg_min_events=0, level_occupancy=0, seg_events_min=0)]
+    for cl, sl, K, smin, occ, kmin in itertools.product(cmp_levels, seg_levels, (256, 512, 1024), (0, 256, 512),
+                                                        (0, 4), (0, 32)):
+        if sl > L and (K != 512 or smin != 0 or kmin != 0):
             continue  # windows never used: one representative
-        out.append(dict(cmp_level=cl, seg_level=sl, seg_events=K, seg_min_events=smin, level_occupancy=occ))
+        out.append(dict(cmp_level=cl, seg_level=sl, seg_events=K, seg_min_events=smin, level_occupancy=occ,
+                        seg_events_min=kmin))
     return out
 
 
