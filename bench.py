@@ -302,12 +302,15 @@ def _oracle_clouds(chunk):
     return out
 
 
-def batched_cpu_baseline(xyz, off, sample: int = ORACLE_BATCH_SAMPLE, workers: int | None = None):
+def batched_cpu_baseline(xyz, off, sample: int = ORACLE_BATCH_SAMPLE, workers: int | None = None,
+                         every_cloud: bool = False):
     """The oracle over the first `sample` clouds of the batch, one cloud at a
     time per worker process on every host core (clouds are independent).  The
     pool is started with `spawn` and warmed up (oracle loaded in each worker)
-    before the timed map.  Returns (baseline dict, {cloud: (faces, digest)});
-    never raises: a failure is reported as unavailable with no digests."""
+    before the timed map.  With every_cloud, the same pool then hulls the rest
+    of the batch, untimed, so that every cloud has a digest.  Returns
+    (baseline dict, {cloud: (faces, digest)}); never raises: a failure is
+    reported as unavailable with no digests."""
     import multiprocessing as mp
 
     try:
@@ -324,8 +327,12 @@ def batched_cpu_baseline(xyz, off, sample: int = ORACLE_BATCH_SAMPLE, workers: i
             t0 = time.perf_counter()
             res = pool.map_async(_oracle_clouds, chunks, chunksize=1).get(timeout=240)
             dt = time.perf_counter() - t0
+            if every_cloud and sample < len(off) - 1:
+                rest = [(b, np.ascontiguousarray(xyz[off[b]: off[b + 1]])) for b in range(sample, len(off) - 1)]
+                res = res + pool.map_async(_oracle_clouds, [rest[i: i + per] for i in range(0, len(rest), per)],
+                                           chunksize=1).get(timeout=600)
         digests = {b: (nf, d) for part in res for b, nf, d in part}
-        done = len(digests)
+        done = min(len(digests), sample)
         return ({"hulls_per_s": done / dt, "cores": workers, "kind": "oracle",
                  "sample": f"first {done} clouds of the batch ({int(off[done] - off[0])} points), one process per core",
                  "seconds": dt}, digests)
@@ -445,7 +452,7 @@ def batched_leg(hull3d, torch, steps: int, cpu_baseline: bool = False, clouds: i
            "per_cloud_plain_hulls_per_s": PLAIN_SAMPLE / (plain_ms / 1e3),
            "per_cloud_plain_sample": PLAIN_SAMPLE}
     if cpu_baseline:
-        out["cpu_baseline"], digests = batched_cpu_baseline(xyz, off)
+        out["cpu_baseline"], digests = batched_cpu_baseline(xyz, off, every_cloud=True)
         out["parity"] = batch_parity(faces, nf, foff, digests)
     return out
 

@@ -59,6 +59,9 @@ def test_batched_oracle_baseline_on_a_small_batch():
     assert r["cores"] == 2 and r["kind"] == "oracle" and r["hulls_per_s"] > 0
     assert r["sample"].startswith("first 64 clouds")
     assert sorted(digests) == list(range(64))
+    r, digests = bench.batched_cpu_baseline(xyz, off, sample=32, workers=2, every_cloud=True)
+    assert r["sample"].startswith("first 32 clouds")  # the timed part
+    assert sorted(digests) == list(range(96))  # every cloud digested for the parity check
 
 
 def test_batch_parity_accepts_the_oracle_faces_and_rejects_a_changed_face():
