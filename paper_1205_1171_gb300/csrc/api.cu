@@ -88,6 +88,9 @@ struct hull3d_plan_s {
     int32_t *status = nullptr;
     int64_t *nfaces = nullptr;
     int64_t *items = nullptr;  // device count of a sort's items (Delaunay triangle keys)
+    // the point sort's long runs of one x-value: [0] the full-sort count (0, or n when the runs do not fit),
+    // [1] the number of long runs (as an int), then their starts and lengths
+    int64_t *sortfb = nullptr;
     int32_t *stage_xyz = nullptr, *stage_faces = nullptr;
     // pinned host mirrors
     int64_t *h_nfaces = nullptr;
@@ -270,6 +273,7 @@ size_t layout(hull3d_plan_s *p, char *base)
     p->status = b.take<int32_t>(1);
     p->nfaces = b.take<int64_t>(1);
     p->items = b.take<int64_t>(1);
+    p->sortfb = b.take<int64_t>(2 + TIE_SORT_LONG_CAP + TIE_SORT_LONG_CAP / 2);
     p->stage_xyz = b.take<int32_t>(3 * N);
     p->stage_faces = b.take<int32_t>(3 * N2);
     return b.off;
@@ -533,9 +537,18 @@ int enqueue_hull(hull3d_plan_s *p, const int32_t *d_xyz, int64_t n, int32_t *d_f
         launch_keys(d_xyz, n, p->k0, p->v0, status, st);
         launches++;
         STEP("keys");
-        which = radix_sort_pairs(p->k0, p->v0, p->k1, p->v1, n, nullptr, 63, p->ss, st, &launches);
+        // by x only (bits 39-62: three passes), then each x-value's few points
+        // by the whole key; a cloud with too many points on one x-value takes
+        // the full 63-bit sort instead (its launches see a zero count otherwise)
+        CK(cudaMemsetAsync(p->sortfb, 0, 2 * sizeof(int64_t), st));
+        radix_sort_pairs(p->k0, p->v0, p->k1, p->v1, n, nullptr, 24, p->ss, st, &launches, 39);
+        const TieRuns runs{ p->sortfb, (int *)(p->sortfb + 1), p->sortfb + 2, (int *)(p->sortfb + 2 + TIE_SORT_LONG_CAP) };
+        launch_tie_sort(p->k1, p->v1, p->k0, p->v0, n, TIE_SORT_MAX_RUN, runs, st);
+        launches += 2;
+        // the full sort of the x-sorted keys ends in (k1, v1) after its even number of passes
+        radix_sort_pairs(p->k1, p->v1, p->k0, p->v0, n, p->sortfb, 63, p->ss, st, &launches);
         STEP("point sort");
-        launch_decode(which ? p->k1 : p->k0, which ? p->v1 : p->v0, n, p->P4, status, st);
+        launch_decode_either(p->k0, p->v0, p->k1, p->v1, p->sortfb, n, p->P4, status, st);
         launches++;
         STEP("decode");
     }

@@ -21,12 +21,34 @@ constexpr int SORT_TILE = 4096;  // keys per CTA tile (256 threads x 16)
 // capacity) by bits [0, bits) of the key.  Ping-pongs between (k0, v0) and
 // (k1, v1); returns 0 if the result ends in (k0, v0) and 1 otherwise.
 int radix_sort_pairs(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int64_t n, const int64_t *d_n,
-                     int bits, const SortScratch &s, cudaStream_t st, int64_t *launches);
+                     int bits, const SortScratch &s, cudaStream_t st, int64_t *launches, int lo_bit = 0);
+// Sorts each run of point keys with one x-value (bits 42-62) by the whole
+// key, from (kin, vin) into (kout, vout): one thread per key of a run of at
+// most max_run keys, one CTA per longer run (up to TIE_SORT_LONG_CAP runs of
+// up to TIE_SORT_LONG_MAX keys); beyond that it stores n in *runs.fallback_n
+// and leaves such runs out (the caller then sorts every key of kin in full).
+// runs.fallback_n and runs.count start at zero (two launches).
+constexpr int TIE_SORT_LONG_MAX = 4096;
+constexpr int TIE_SORT_LONG_CAP = 256;
+struct TieRuns {
+    int64_t *fallback_n;
+    int *count;
+    int64_t *start;  // [TIE_SORT_LONG_CAP]
+    int *len;        // [TIE_SORT_LONG_CAP]
+};
+void launch_tie_sort(const uint64_t *kin, const uint32_t *vin, uint64_t *kout, uint32_t *vout, int64_t n, int max_run,
+                     const TieRuns &runs, cudaStream_t st);
+// launch_decode from (keys_b, vals_b) instead where *use_b is nonzero.
+void launch_decode_either(const uint64_t *keys, const uint32_t *vals, const uint64_t *keys_b, const uint32_t *vals_b,
+                          const int64_t *use_b, int64_t n, int4 *P, int32_t *status, cudaStream_t st);
 
 // A1 + A2 for n <= SMALL_SORT_MAX in one CTA (keys, bitonic sort in shared
 // memory, decode, duplicates), and the canonical sort of such a hull's faces
 // (keys and values as for launch_face_out; *d_nf <= 2 SMALL_SORT_MAX).
 constexpr int SMALL_SORT_MAX = 4096;
+// Longest run of points on one x-value the point sort orders in place after
+// its x passes (larger runs: the full sort).
+constexpr int TIE_SORT_MAX_RUN = 128;
 constexpr int SMALL_SORT_THREADS = 1024;
 void launch_small_sort(const int32_t *xyz, int64_t n, int4 *P, int32_t *status, cudaStream_t st);
 void launch_small_face_sort(const uint64_t *keys, const uint32_t *vals, int fbits, const int64_t *d_nf,

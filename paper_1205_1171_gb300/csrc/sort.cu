@@ -34,11 +34,17 @@ void launch_keys(const int32_t *xyz, int64_t n, uint64_t *keys, uint32_t *vals, 
     k_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(xyz, n, keys, vals, status);
 }
 
+// (keys, vals), or (keys_b, vals_b) where *use_b is nonzero
 __global__ void k_decode(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t n,
-                         int4 *__restrict__ P, int32_t *status)
+                         int4 *__restrict__ P, int32_t *status, const uint64_t *keys_b, const uint32_t *vals_b,
+                         const int64_t *use_b)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (use_b && *use_b) {
+        keys = keys_b;
+        vals = vals_b;
+    }
     uint64_t k = keys[i];
     const int lo = -(1 << 20);
     P[i] = make_int4((int)((k >> 42) & 0x1fffff) + lo, (int)(k & 0x1fffff) + lo, (int)((k >> 21) & 0x1fffff) + lo,
@@ -49,7 +55,75 @@ __global__ void k_decode(const uint64_t *__restrict__ keys, const uint32_t *__re
 void launch_decode(const uint64_t *keys, const uint32_t *vals, int64_t n, int4 *P, int32_t *status, cudaStream_t st)
 {
     if (n <= 0) return;
-    k_decode<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(keys, vals, n, P, status);
+    k_decode<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(keys, vals, n, P, status, nullptr, nullptr, nullptr);
+}
+
+void launch_decode_either(const uint64_t *keys, const uint32_t *vals, const uint64_t *keys_b, const uint32_t *vals_b,
+                          const int64_t *use_b, int64_t n, int4 *P, int32_t *status, cudaStream_t st)
+{
+    if (n <= 0) return;
+    k_decode<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(keys, vals, n, P, status, keys_b, vals_b, use_b);
+}
+
+// The point keys after a radix sort of their x bits (42-62) only: each run of
+// equal x holds the points of one x-value in input order.  Each key of a run
+// of at most max_run keys takes its place in the run by rank: the number of
+// the run's keys below it, ties by position (equal keys are duplicate points,
+// which the decode reports), and moves from (kin, vin) to (kout, vout) there.
+// The threads only read the input, so the runs need no ordering among them.
+// On uniform clouds a run holds the few points that share an x-value (eight
+// on average at 2^24 points).  The first key of a longer run puts the run on
+// the list that k_tie_sort_long sorts one per CTA (a clipped Gaussian puts
+// hundreds of points on each clipping plane); a run longer than
+// TIE_SORT_LONG_MAX, or more than TIE_SORT_LONG_CAP long runs, ask for the
+// full sort instead.
+__global__ void k_tie_sort(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+                           uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n, int max_run,
+                           TieRuns runs)
+{
+    const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    const uint64_t k = kin[a], x = k >> 42;
+    int64_t i = a;  // the run's first key, looked for at most max_run back
+    while (i > 0 && a - i <= max_run && (kin[i - 1] >> 42) == x) i--;
+    if (a - i > max_run) return;  // in a long run: its first key registers it
+    int64_t e = a + 1;
+    const int64_t lim = i == a ? TIE_SORT_LONG_MAX : max_run;  // the first key measures long runs too
+    while (e < n && e - i <= lim && (kin[e] >> 42) == x) e++;
+    if (e - i > max_run) {
+        if (i == a) {
+            const int slot = e - i <= TIE_SORT_LONG_MAX ? atomicAdd(runs.count, 1) : TIE_SORT_LONG_CAP;
+            if (slot < TIE_SORT_LONG_CAP) {
+                runs.start[slot] = i;
+                runs.len[slot] = (int)(e - i);
+            } else {
+                *runs.fallback_n = n;
+            }
+        }
+        return;
+    }
+    int64_t r = i;
+    for (int64_t b = i; b < e; b++) {
+        const uint64_t kb = kin[b];
+        r += (kb < k) | (kb == k && b < a);
+    }
+    kout[r] = k;
+    vout[r] = vin[a];
+}
+
+// The long runs of k_tie_sort, one per CTA at a time: the run's keys in shared
+// memory, padded to a power of two with the largest key, a bitonic sort, and
+// the run written to the output buffer.
+__global__ void __launch_bounds__(1024) k_tie_sort_long(const uint64_t *__restrict__ kin,
+                                                        const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
+                                                        uint32_t *__restrict__ vout, TieRuns runs);
+
+void launch_tie_sort(const uint64_t *kin, const uint32_t *vin, uint64_t *kout, uint32_t *vout, int64_t n, int max_run,
+                     const TieRuns &runs, cudaStream_t st)
+{
+    if (n <= 0) return;
+    k_tie_sort<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(kin, vin, kout, vout, n, max_run, runs);
+    k_tie_sort_long<<<64, 1024, 0, st>>>(kin, vin, kout, vout, runs);
 }
 
 // ---------------------------------------------------------------------------
@@ -73,6 +147,32 @@ __device__ void bitonic_block(uint64_t *k, V *v, int m)
             }
             __syncthreads();
         }
+}
+
+__global__ void __launch_bounds__(1024) k_tie_sort_long(const uint64_t *__restrict__ kin,
+                                                        const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
+                                                        uint32_t *__restrict__ vout, TieRuns runs)
+{
+    __shared__ uint64_t K[TIE_SORT_LONG_MAX];
+    __shared__ uint32_t V[TIE_SORT_LONG_MAX];
+    const int cnt = min(*runs.count, TIE_SORT_LONG_CAP);
+    for (int r = blockIdx.x; r < cnt; r += gridDim.x) {
+        const int64_t s = runs.start[r];
+        const int len = runs.len[r];
+        int m = 1;
+        while (m < len) m <<= 1;
+        for (int t = threadIdx.x; t < m; t += blockDim.x) {
+            K[t] = t < len ? kin[s + t] : ~0ull;
+            V[t] = t < len ? vin[s + t] : 0u;
+        }
+        __syncthreads();
+        bitonic_block(K, V, m);
+        for (int t = threadIdx.x; t < len; t += blockDim.x) {
+            kout[s + t] = K[t];
+            vout[s + t] = V[t];
+        }
+        __syncthreads();
+    }
 }
 
 __global__ void __launch_bounds__(SMALL_SORT_THREADS) k_small_sort(const int32_t *__restrict__ xyz, int n,
@@ -398,7 +498,7 @@ void sort_kernel_attributes()
 }
 
 int radix_sort_pairs(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int64_t n, const int64_t *d_n,
-                     int bits, const SortScratch &s, cudaStream_t st, int64_t *launches)
+                     int bits, const SortScratch &s, cudaStream_t st, int64_t *launches, int lo_bit)
 {
     if (n <= 0) return 0;
     int64_t T = (n + SORT_TILE - 1) / SORT_TILE;
@@ -414,7 +514,7 @@ int radix_sort_pairs(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int
     uint64_t *ka = k0, *kb = k1;
     uint32_t *va = v0, *vb = v1;
     for (int p = 0; p < passes; p++) {
-        int shift = 8 * p;
+        int shift = lo_bit + 8 * p;
         k_rs_hist<<<G, RS_THREADS, 0, st>>>(ka, n, d_n, shift, s.hist, T);
         k_rs_rowscan<<<256, 1024, 0, st>>>(s.hist, T, d_n, n, s.rowsum);
         k_rs_scatter<<<G, RS_THREADS, RS_STAGE_BYTES, st>>>(ka, va, kb, vb, n, d_n, shift, s.hist, T, s.rowsum);

@@ -186,6 +186,33 @@ def test_float_time_filter_on_and_off_agree(H, filter_level):
         p.close()
 
 
+@pytest.mark.parametrize("per_x", [1, 8, 128, 129, 1500, 5000])
+def test_point_sort_runs_of_equal_x(H, plan, per_x):
+    """The point sort orders by x, then each x-value's run of points by z and
+    y in place: one thread per run of up to 128 points, one CTA per longer
+    run, and the full sort for a run above 4096 points.  Clouds of
+    6000 points whose x-values hold `per_x` points each (and one cloud
+    mixing them with a uniform cube) give the oracle's faces, and a duplicate inside a
+    run is reported."""
+    rng = np.random.default_rng(per_x)
+    n = 6000
+    xs = rng.choice(np.arange(-(1 << 19), 1 << 19), size=(n + per_x - 1) // per_x, replace=False)
+    x = np.repeat(xs, per_x)[:n]
+    pts = np.stack([x, rng.integers(-(1 << 20), 1 << 20, n), rng.integers(-(1 << 20), 1 << 20, n)], 1)
+    pts = np.unique(pts, axis=0).astype(np.int32)
+    pts = pts[rng.permutation(len(pts))]
+    assert np.array_equal(run(plan, pts), oracle.hull(pts))
+    mixed = np.concatenate([pts[: len(pts) // 2], inputs.cloud_seeded("cube", 4000, 17)])
+    mixed = np.unique(mixed, axis=0).astype(np.int32)
+    mixed = mixed[rng.permutation(len(mixed))]
+    assert np.array_equal(run(plan, mixed), oracle.hull(mixed))
+    dup = pts.copy()
+    dup[-1] = dup[0]
+    with pytest.raises(H.Hull3DError) as e:
+        run(plan, dup)
+    assert e.value.code == H.ERR_DUPLICATE
+
+
 def test_config_small_cube_4096(plan):
     pts = inputs.cloud_seeded("cube", 4096, inputs.seed_for(1))
     got = run(plan, pts)
