@@ -77,38 +77,56 @@ void launch_decode_either(const uint64_t *keys, const uint32_t *vals, const uint
 // hundreds of points on each clipping plane); a run longer than
 // TIE_SORT_LONG_MAX, or more than TIE_SORT_LONG_CAP long runs, ask for the
 // full sort instead.
-__global__ void k_tie_sort(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
-                           uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n, int max_run,
-                           TieRuns runs)
+constexpr int TIE_TILE = 2048;     // keys ranked per CTA
+constexpr int TIE_THREADS = 256;
+constexpr int TIE_HALO = 128;      // = TIE_SORT_MAX_RUN: a short run around the tile lies in the tile and its halos
+
+__global__ void __launch_bounds__(TIE_THREADS) k_tie_sort(const uint64_t *__restrict__ kin,
+                                                         const uint32_t *__restrict__ vin,
+                                                         uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                         int64_t n, int max_run, TieRuns runs)
 {
-    const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (a >= n) return;
-    const uint64_t k = kin[a], x = k >> 42;
-    int64_t i = a;  // the run's first key, looked for at most max_run back
-    while (i > 0 && a - i <= max_run && (kin[i - 1] >> 42) == x) i--;
-    if (a - i > max_run) return;  // in a long run: its first key registers it
-    int64_t e = a + 1;
-    const int64_t lim = i == a ? TIE_SORT_LONG_MAX : max_run;  // the first key measures long runs too
-    while (e < n && e - i <= lim && (kin[e] >> 42) == x) e++;
-    if (e - i > max_run) {
-        if (i == a) {
-            const int slot = e - i <= TIE_SORT_LONG_MAX ? atomicAdd(runs.count, 1) : TIE_SORT_LONG_CAP;
-            if (slot < TIE_SORT_LONG_CAP) {
-                runs.start[slot] = i;
-                runs.len[slot] = (int)(e - i);
-            } else {
-                *runs.fallback_n = n;
+    // the tile's keys and max_run more on each side, in shared memory
+    __shared__ uint64_t K[TIE_TILE + 2 * TIE_HALO];
+    const int64_t t0 = (int64_t)blockIdx.x * TIE_TILE;
+    const int64_t b0 = t0 - TIE_HALO;
+    for (int t = threadIdx.x; t < TIE_TILE + 2 * TIE_HALO; t += TIE_THREADS) {
+        const int64_t g = b0 + t;
+        K[t] = (g >= 0 && g < n) ? kin[g] : ~0ull;  // outside: never on a run (x bits all ones are out of range)
+    }
+    __syncthreads();
+    for (int u = threadIdx.x; u < TIE_TILE; u += TIE_THREADS) {
+        const int64_t a = t0 + u;
+        if (a >= n) break;
+        const int ia = u + TIE_HALO;  // a's slot
+        const uint64_t k = K[ia], x = k >> 42;
+        int i = ia;  // the run's first key, looked for at most max_run back
+        while (i > 0 && ia - i <= max_run && (K[i - 1] >> 42) == x) i--;
+        if (ia - i > max_run) continue;  // in a long run: its first key registers it
+        int e = ia + 1;
+        while (e < TIE_TILE + 2 * TIE_HALO && e - i <= max_run && (K[e] >> 42) == x) e++;
+        if (e - i > max_run) {
+            if (i == ia) {  // the first key measures the run in global memory and registers it
+                int64_t ge = a + (e - i);
+                while (ge < n && ge - a <= TIE_SORT_LONG_MAX && (kin[ge] >> 42) == x) ge++;
+                const int slot = ge - a <= TIE_SORT_LONG_MAX ? atomicAdd(runs.count, 1) : TIE_SORT_LONG_CAP;
+                if (slot < TIE_SORT_LONG_CAP) {
+                    runs.start[slot] = a;
+                    runs.len[slot] = (int)(ge - a);
+                } else {
+                    *runs.fallback_n = n;
+                }
             }
+            continue;
         }
-        return;
+        int r = 0;
+        for (int b = i; b < e; b++) {
+            const uint64_t kb = K[b];
+            r += (kb < k) | (kb == k && b < ia);
+        }
+        kout[a - (ia - i) + r] = k;
+        vout[a - (ia - i) + r] = vin[a];
     }
-    int64_t r = i;
-    for (int64_t b = i; b < e; b++) {
-        const uint64_t kb = kin[b];
-        r += (kb < k) | (kb == k && b < a);
-    }
-    kout[r] = k;
-    vout[r] = vin[a];
 }
 
 // The long runs of k_tie_sort, one per CTA at a time: the run's keys in shared
@@ -122,7 +140,9 @@ void launch_tie_sort(const uint64_t *kin, const uint32_t *vin, uint64_t *kout, u
                      const TieRuns &runs, cudaStream_t st)
 {
     if (n <= 0) return;
-    k_tie_sort<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(kin, vin, kout, vout, n, max_run, runs);
+    k_tie_sort<<<(unsigned)((n + TIE_TILE - 1) / TIE_TILE), TIE_THREADS, 0, st>>>(kin, vin, kout, vout, n,
+                                                                                   max_run < TIE_HALO ? max_run : TIE_HALO,
+                                                                                   runs);
     k_tie_sort_long<<<64, 1024, 0, st>>>(kin, vin, kout, vout, runs);
 }
 
