@@ -85,8 +85,9 @@ typedef struct {
                                  arithmetic of the paper's GPU kernel (Sec. 3: cl_float coordinates) instead
                                  of the exact predicates -- an ablation: the result need not be the hull,
                                  and is the only knob here that can change it.  0: exact (default) */
-    int32_t seg_slots_big;   /* shared-memory table size of the second round of time windows (<= 6144, automatic:
-                                6144); windows too large for it get slot tables in global memory */
+    int32_t seg_slots_big;   /* shared-memory table size of the third round of time windows (<= 6144, automatic:
+                                6144; the second round's holds 3072, or this many if fewer); windows too large
+                                for it get slot tables in global memory */
     int32_t filter_level;    /* first merge level of the thread-per-merge kernel whose time comparisons try a
                                 float filter before the exact products (the result is the same; automatic: 3 up
                                 to 2^21 points, log2(n) - 15 above, where points share x-values) */
@@ -274,7 +275,8 @@ int hull3d_level_events(hull3d_plan_t plan, int64_t *out);
  *     windowed merge of the level then ran serially)
  *   1 merges cut into windows
  *   2 windows
- *   3 windows retried with the larger shared-memory table
+ *   3 windows retried with the larger shared-memory tables (3072, then
+ *     seg_slots_big slots)
  *   4 windows run with a slot table in global memory
  *   5 merges that fit no table and ran serially (one thread each)
  *   6 the window-length multiplier of a second attempt, taken when the

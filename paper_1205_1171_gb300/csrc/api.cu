@@ -225,6 +225,7 @@ size_t layout(hull3d_plan_s *p, char *base)
                 sb.wlist = b.take<unsigned>(2 * p->S_cap);
                 sb.flist = b.take<unsigned>(2 * p->S_cap);
                 sb.glist = b.take<unsigned>(2 * p->S_cap);
+                sb.flist2 = b.take<unsigned>(2 * p->S_cap);
                 sb.mlist = b.take<unsigned>(2 * p->M_cap);
             }
         }

@@ -20,7 +20,9 @@ struct SegArgs {
     // device work lists (entries: pass << 31 | index)
     unsigned *wlist, *flist, *mlist;  // windows, windows to retry, merges in windows
     int *wcount, *fcount;
-    // windows too large for the biggest shared-memory table: a third round
+    unsigned *flist2;  // windows for the largest shared-memory table
+    int *f2count;
+    // windows too large for the biggest shared-memory table: a last round
     // with per-CTA slot tables of gcap slots in global memory (gtab, gstride
     // bytes apart); none when gtab is null
     unsigned *glist;
@@ -296,26 +298,27 @@ __device__ __forceinline__ int64_t lower_key(const uint64_t *keys, int64_t cnt, 
 
 // retry = 0: every window, slot table of geo.scap in shared memory; a window
 // that does not fit goes to the retry list.  retry = 1: those windows, with a
-// shared-memory table of scap_big; retry = 2: the ones that still did not
-// fit, with a table of gcap slots in global memory.  A window that fits none
-// sends its merge to the serial fallback.
-__device__ void seg_window(const SegArgs &a, int pass, int64_t g, int retry, int scap_big);
+// shared-memory table of `cap` slots (two CTAs per SM); retry = 2: the ones
+// that still did not fit, with the largest shared-memory table (one CTA per
+// SM); retry = 3: the rest, with a table of `cap` slots in global memory.  A
+// window that fits none sends its merge to the serial fallback.
+__device__ void seg_window(const SegArgs &a, int pass, int64_t g, int retry, int cap);
 
-__global__ void __launch_bounds__(SEG_THREADS) k_seg_merge(SegArgs a, int retry, int scap_big)
+__global__ void __launch_bounds__(SEG_THREADS) k_seg_merge(SegArgs a, int retry, int cap)
 {
     if (*a.status) return;
-    const unsigned *list = retry == 2 ? a.glist : retry ? a.flist : a.wlist;
-    const int cnt = retry == 2 ? *a.gcount : retry ? *a.fcount : *a.wcount;
+    const unsigned *list = retry == 3 ? a.glist : retry == 2 ? a.flist2 : retry ? a.flist : a.wlist;
+    const int cnt = retry == 3 ? *a.gcount : retry == 2 ? *a.f2count : retry ? *a.fcount : *a.wcount;
     for (int it = blockIdx.x; it < cnt; it += gridDim.x) {
         const unsigned e = list[it];
-        seg_window(a, (int)(e >> 31), (int64_t)(e & 0x7fffffffu), retry, scap_big);
+        seg_window(a, (int)(e >> 31), (int64_t)(e & 0x7fffffffu), retry, cap);
         __syncthreads();
     }
 }
 
 // One window: its start hulls and inserted points in a slot table, the start
 // bridge, the event loop.  All threads of the (one-warp) CTA call it.
-__device__ void seg_window(const SegArgs &a, int pass, int64_t g, int retry, int scap_big)
+__device__ void seg_window(const SegArgs &a, int pass, int64_t g, int retry, int cap)
 {
     extern __shared__ int sm[];
     __shared__ int s_bad, s_nins;
@@ -334,7 +337,7 @@ __device__ void seg_window(const SegArgs &a, int pass, int64_t g, int retry, int
     const int S = sb.nseg[m];
     if (s >= S) return;
     if (*a.overflow) { if (threadIdx.x == 0) sb.nofit[m] = 1; return; }
-    const int scap = retry == 2 ? a.gcap : retry ? scap_big : G.scap;
+    const int scap = retry ? cap : G.scap;
     const int evcap = retry ? SEG_EVCAP_BIG : G.K;  // child events the window's table holds
     const int tid = threadIdx.x;
     const int src = (G.level - 1) & 1;
@@ -370,13 +373,14 @@ __device__ void seg_window(const SegArgs &a, int pass, int64_t g, int retry, int
         if (tid == 0) {
             const unsigned e = ((unsigned)pass << 31) | (unsigned)g;
             if (retry == 0) a.flist[atomicAdd(a.fcount, 1)] = e;
-            else if (retry == 1 && a.gtab) a.glist[atomicAdd(a.gcount, 1)] = e;
+            else if (retry == 1) a.flist2[atomicAdd(a.f2count, 1)] = e;
+            else if (retry == 2 && a.gtab) a.glist[atomicAdd(a.gcount, 1)] = e;
             else sb.nofit[m] = 1;
         }
         return;
     }
-    // the slot table: this CTA's region of global memory in the third round
-    int4 *sPt = retry == 2 ? (int4 *)(a.gtab + (int64_t)blockIdx.x * a.gstride) : (int4 *)sm;
+    // the slot table: this CTA's region of global memory in the last round
+    int4 *sPt = retry == 3 ? (int4 *)(a.gtab + (int64_t)blockIdx.x * a.gstride) : (int4 *)sm;
     int2 *sLk = (int2 *)(sPt + scap);
     int *sRK = (int *)(sLk + scap);
     unsigned *sIn = (unsigned *)(sRK + scap);  // window movies as slots: left then right
@@ -632,6 +636,8 @@ void launch_seg_level(const Points &pts, const Span &sp, int level, PassBufs *pa
     a.refit = overflow + 6;
     a.wlist = sbufs[0].wlist;
     a.flist = sbufs[0].flist;
+    a.flist2 = sbufs[0].flist2;
+    a.f2count = overflow + 7;
     a.mlist = sbufs[0].mlist;
     a.glist = sbufs[0].glist;
     a.gtab = gt.base;
@@ -667,10 +673,14 @@ void launch_seg_level(const Points &pts, const Span &sp, int level, PassBufs *pa
     // SM (small tables fit that many; registers allow about 9)
     const int wg = flat_grid * 4;
     k_seg_merge<<<wg, SEG_THREADS, seg_smem_bytes(scap, K), st>>>(a, 0, scap);
+    const int mid = scap_big < SEG_SLOTS_MID ? scap_big : SEG_SLOTS_MID;
+    k_seg_merge<<<flat_grid / 2 > 0 ? flat_grid / 2 : 1, SEG_THREADS, seg_smem_bytes(mid, SEG_EVCAP_BIG), st>>>(
+        a, 1, mid);
     k_seg_merge<<<flat_grid / 4 > 0 ? flat_grid / 4 : 1, SEG_THREADS, seg_smem_bytes(scap_big, SEG_EVCAP_BIG), st>>>(
-        a, 1, scap_big);
+        a, 2, scap_big);
+    *launches += 1;
     if (gt.base) {
-        k_seg_merge<<<gt.ctas, SEG_THREADS, 0, st>>>(a, 2, gt.cap);
+        k_seg_merge<<<gt.ctas, SEG_THREADS, 0, st>>>(a, 3, gt.cap);
         *launches += 1;
     }
     k_seg_concat<<<flat_grid, CAT_THREADS, 0, st>>>(a);

@@ -46,6 +46,7 @@ struct SegBufs {
     int *nofit;             // [M_cap]: 1 when a window did not fit (merge serially)
     unsigned *wlist, *flist, *mlist;  // work lists (pass 0's copy holds both passes): [2 S_cap], [2 S_cap], [2 M_cap]
     unsigned *glist;                  // [2 S_cap]: windows for the global-memory slot tables
+    unsigned *flist2;                 // [2 S_cap]: windows for the largest shared-memory table
 };
 
 // Geometry of one segment level (shared by both passes).
@@ -60,7 +61,11 @@ struct SegGeom {
     int min_events;  // merges with at most this many child events are not merged here
 };
 
-// Child events a window of the retry rounds (the large shared-memory table and
+// Slots of the middle retry round's shared-memory table (two per SM), when
+// the largest one is at least this large.
+constexpr int SEG_SLOTS_MID = 3072;
+
+// Child events a window of the retry rounds (the larger shared-memory tables and
 // the global-memory tables) holds; the first round holds the level's longest
 // window K.
 constexpr int SEG_EVCAP_BIG = 4096;
