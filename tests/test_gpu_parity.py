@@ -99,12 +99,14 @@ def test_segment_parallel_levels_agree(H, seg_level, seg_events, seg_slots, seg_
         p.close()
 
 
-@pytest.mark.parametrize("seg_slots_big", [48, 96])
+@pytest.mark.parametrize("seg_slots_big", [48, 96, 0])
 def test_windows_beyond_the_shared_memory_tables_use_global_tables(H, seg_slots_big):
-    """Windows whose start hulls fit neither shared-memory slot table (both
-    made tiny here) run with slot tables in global memory, with the oracle's
+    """Windows whose start hulls fit no shared-memory slot table (all made
+    tiny here) run with slot tables in global memory, with the oracle's
     faces; hull-heavy clouds (the sphere) put nearly every window there.
-    The window counters say where each window ran."""
+    With the default larger tables (seg_slots_big = 0) the retry rounds in
+    shared memory take them all.  The window counters say where each window
+    ran."""
     p = H.Hull3D(1 << 16, seg_level=8, seg_slots=32, seg_slots_big=seg_slots_big, seg_events=256, seg_events_min=16)
     col = {k: i for i, k in enumerate(H.WINDOW_STATS)}
     try:
@@ -120,8 +122,10 @@ def test_windows_beyond_the_shared_memory_tables_use_global_tables(H, seg_slots_
                     assert ws[:, col["pair_overflow"]].sum() == 0 and ws[:, col["serial"]].sum() == 0, (dist, n)
                     assert (ws[:, col["global_tables"]] <= ws[:, col["retried"]]).all()
                     assert (ws[:, col["retried"]] <= ws[:, col["windows"]]).all()
-                    if dist == "sphere":
+                    if dist == "sphere" and seg_slots_big:
                         assert ws[:, col["global_tables"]].sum() > 0, ws[8:17].tolist()
+                    if dist == "sphere" and not seg_slots_big:
+                        assert ws[:, col["retried"]].sum() > 0 and ws[:, col["global_tables"]].sum() == 0
     finally:
         p.close()
 
