@@ -70,9 +70,9 @@ ISSUE_PER_SM_PER_CYCLE = 4
 # is the same draw, so its counts scale with the clouds.
 BATCH_SOURCES = ("paper_1205_1171_gb300/csrc/batch.cu", "paper_1205_1171_gb300/csrc/merge.cuh",
                  "paper_1205_1171_gb300/csrc/predicates.cuh")
-BATCH_COUNTS = {"clouds": 4096, "dram_bytes": 58100992, "warp_inst": 7451539633, "thread_inst": 117389443396,
+BATCH_COUNTS = {"clouds": 4096, "dram_bytes": 60569088, "warp_inst": 7648474235, "thread_inst": 124714875403,
                 "knobs": {"batch_warp_nodes": 16},
-                "sources_sha256": "dfee9df38b6d97f09c7af2ac2f1d1b4df639ee77aa0c934d35dfab745aac0527"}
+                "sources_sha256": "0e8bd20198bf60be29fc0f2d9584b43395aab8b702099997ccb5804485af05a0"}
 
 
 def sources_sha256(files=None) -> str:
