@@ -33,6 +33,7 @@ struct SegArgs {
     int64_t gstride;
     int gcap;
     int64_t S_cap, M_cap;
+    int rbits;  // bits of a rank in a start-hull entry's key
     int32_t *status;
 };
 
@@ -84,10 +85,10 @@ __global__ void k_seg_bounds(SegArgs a, int second)
     int cnt = 2 + (ext[1] != ext[0]) + (ext[3] != ext[2]);
     unsigned long long pos = atomicAdd(a.npairs, (unsigned long long)cnt);
     if (pos + cnt > (unsigned long long)G.pair_cap) { atomicExch(a.overflow, 1); return; }
-    a.pairs[pos++] = seg_key(pass, g, 0, ext[0], a.S_cap);
-    if (ext[1] != ext[0]) a.pairs[pos++] = seg_key(pass, g, 0, ext[1], a.S_cap);
-    a.pairs[pos++] = seg_key(pass, g, 1, ext[2], a.S_cap);
-    if (ext[3] != ext[2]) a.pairs[pos++] = seg_key(pass, g, 1, ext[3], a.S_cap);
+    a.pairs[pos++] = seg_key(pass, g, 0, ext[0], a.S_cap, a.rbits);
+    if (ext[1] != ext[0]) a.pairs[pos++] = seg_key(pass, g, 0, ext[1], a.S_cap, a.rbits);
+    a.pairs[pos++] = seg_key(pass, g, 1, ext[2], a.S_cap, a.rbits);
+    if (ext[3] != ext[2]) a.pairs[pos++] = seg_key(pass, g, 1, ext[3], a.S_cap, a.rbits);
 }
 
 // Maps a position q of the level's source movie buffer to its child movie:
@@ -262,7 +263,7 @@ __device__ void seg_pairs_one(const SegArgs &a, int pass, int64_t q, bool valid)
         return;
     }
     unsigned long long pos = base + (unsigned long long)(incl - cnt);
-    for (int s = s_first; s < s_first + cnt; s++) a.pairs[pos++] = seg_key(pass, m * G.smax + s, child, rk, a.S_cap);
+    for (int s = s_first; s < s_first + cnt; s++) a.pairs[pos++] = seg_key(pass, m * G.smax + s, child, rk, a.S_cap, a.rbits);
 }
 
 // ---- merge: one warp per window ---------------------------------------------
@@ -348,9 +349,9 @@ __device__ void seg_window(const SegArgs &a, int pass, int64_t g, int retry, int
     const int wl = b1.x - b0.x, wr = b1.y - b0.y;
     // start hulls
     const int64_t np = (int64_t)*a.npairs;
-    const int64_t aL0 = lower_key(a.pairs, np, seg_key(pass, g, 0, 0, a.S_cap));
-    const int64_t aR0 = lower_key(a.pairs, np, seg_key(pass, g, 1, 0, a.S_cap));
-    const int64_t aR1 = lower_key(a.pairs, np, seg_key(pass, g + 1, 0, 0, a.S_cap));
+    const int64_t aL0 = lower_key(a.pairs, np, seg_key(pass, g, 0, 0, a.S_cap, a.rbits));
+    const int64_t aR0 = lower_key(a.pairs, np, seg_key(pass, g, 1, 0, a.S_cap, a.rbits));
+    const int64_t aR1 = lower_key(a.pairs, np, seg_key(pass, g + 1, 0, 0, a.S_cap, a.rbits));
     const int aL = (int)(aR0 - aL0), aR = (int)(aR1 - aR0);
     // inserted points of the window
     if (tid == 0) { s_bad = 0; s_nins = 0; }
@@ -387,7 +388,7 @@ __device__ void seg_window(const SegArgs &a, int pass, int64_t g, int retry, int
     // start hulls, linked in x-order
     for (int i = tid; i < aL + aR; i += SEG_THREADS) {
         const bool left = i < aL;
-        const int r = (int)(a.pairs[aL0 + i] & ((1ull << 28) - 1));
+        const int r = (int)(a.pairs[aL0 + i] & ((1ull << a.rbits) - 1));
         sRK[i] = r;
         sPt[i] = a.pts.P[r];
         const int first = left ? 0 : aL, last = left ? aL - 1 : aL + aR - 1;
@@ -625,6 +626,8 @@ void launch_seg_level(const Points &pts, const Span &sp, int level, PassBufs *pa
     a.overflow = overflow;
     a.S_cap = S_cap;
     a.M_cap = M_cap;
+    a.rbits = 1;  // the ranks of the rank space: below n
+    while ((1ll << a.rbits) < n) a.rbits++;
     a.status = status;
     const int64_t M = (n + (1ll << level) - 1) >> level;
     const int64_t G = M * a.geo.smax;
@@ -663,8 +666,8 @@ void launch_seg_level(const Points &pts, const Span &sp, int level, PassBufs *pa
     k_seg_bounds<<<dim3((unsigned)((G + 127) / 128), 2), 128, 0, st>>>(a, 1);
     k_seg_pairs<<<(unsigned)fg, 256, 0, st>>>(a, 1);
     *launches += 6;
-    int key_bits = 28;
-    while ((1ll << (key_bits - 28)) < 4 * S_cap) key_bits++;
+    int key_bits = a.rbits;
+    while ((1ll << (key_bits - a.rbits)) < 4 * S_cap) key_bits++;
     int which = radix_sort_pairs(pairs, pair_vals, pairs_alt, vals_alt, pair_cap, (const int64_t *)npairs, key_bits, ss,
                                  st, launches);
     a.pairs = which ? pairs_alt : pairs;

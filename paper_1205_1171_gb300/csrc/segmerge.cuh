@@ -108,10 +108,11 @@ __host__ __device__ __forceinline__ int seg_count(int nl, int nr, int K, int sma
     return s < smax ? s : smax;
 }
 
-// Key of a start-hull entry: pass, window, child, rank (sorted ascending).
-__host__ __device__ __forceinline__ uint64_t seg_key(int pass, int64_t g, int child, int rank, int64_t S_cap)
+// Key of a start-hull entry: pass, window, child, rank (sorted ascending);
+// the rank takes the low rbits bits (ranks of the rank space are below 2^rbits).
+__host__ __device__ __forceinline__ uint64_t seg_key(int pass, int64_t g, int child, int rank, int64_t S_cap, int rbits)
 {
-    return ((((uint64_t)pass * (uint64_t)S_cap + (uint64_t)g) * 2u + (uint64_t)child) << 28) | (uint64_t)rank;
+    return ((((uint64_t)pass * (uint64_t)S_cap + (uint64_t)g) * 2u + (uint64_t)child) << rbits) | (uint64_t)rank;
 }
 
 // The time of child event k of a movie (its triple, in ranks).
